@@ -1,0 +1,342 @@
+"""Benchmark of the HTLR matrix-vector product (HMultVec) on GB300.
+
+Default workload (N=1): d=3, n=32 (N=32768), kernel 1/|x-y|, a(x)=1+0.5 sin(2 pi x_1),
+leaf 4^3, Chebyshev order p=5, eta=1, one FP64 right-hand side u ~ N(0,1) (seeded),
+STORED layout (one core per admissible block, one dense matrix per inadmissible leaf).
+The operator is constructed once (Algorithm 1); a step is one HMultVec (Algorithm 2)
+over the whole operator: upward contractions, the stream over every core and dense
+block, reductions and the downward expansion into f.
+
+Prints one JSON line.  ``--impl reference`` times the CPU oracle (FP64 C, host cores)
+on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "HTLR matvec Gpts*RHS/s"
+UNIT = "Gpts*RHS/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="htlr", choices=["htlr", "reference"])
+    ap.add_argument("--config", default="c2")
+    ap.add_argument("--storage", type=int, default=1, help="1 STORED, 2 SHARED, 0 AUTO")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-s", type=float, default=20.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_desc(w, storage_name):
+    kern = {0: "log|x-y|", 1: "1/|x-y|", 2: "exp(-|x-y|)", 3: "gauss", 4: "poly", 5: "const"}[w.ktype]
+    return (f"{w.name}: d={w.d} n={w.n} N={w.N} kernel {kern} a={w.a_kind} leaf {w.leaf}^{w.d} "
+            f"p={w.p} eta={w.eta:.4g} nrhs={w.nrhs} FP64 {storage_name}")
+
+
+# ----------------------------------------------------------------------------------
+# clocks sampled with nvidia-smi during the timed region
+# ----------------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1].split()[0]))
+                smax.append(float(parts[2].split()[0]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------------
+# CPU oracle timing (reference arm and cpu_baseline leg)
+# ----------------------------------------------------------------------------------
+def time_oracle(w, budget_s):
+    """Times the oracle's HMultVec (Algorithm 2, block by block) on this workload after its
+    construction.  Returns (Gpts*RHS/s, cores, sample description, seconds)."""
+    import oracle
+    t0 = time.perf_counter()
+    H = oracle.HTLR(w.d, w.n, w.ktype, w.leaf, w.p, w.eta, a=w.a(), scale=w.kscale,
+                    param=w.kparam)
+    t_con = time.perf_counter() - t0
+    u = w.u(nrhs=1)
+    times = []
+    t_start = time.perf_counter()
+    while True:
+        t1 = time.perf_counter()
+        H.matvec(u)
+        times.append(time.perf_counter() - t1)
+        if time.perf_counter() - t_start > budget_s or len(times) >= 50:
+            break
+    H.free()
+    t = statistics.median(times)
+    val = w.N * 1 / t / 1e9
+    sample = (f"oracle construct {t_con:.1f} s (OpenMP, {oracle.num_threads()} threads) then "
+              f"{len(times)} single-threaded HMultVec calls on the full workload, 1 RHS, "
+              f"median {t * 1e3:.1f} ms")
+    return val, 1, sample, t
+
+
+def run_reference(args, w):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    budget = max(2.0, args.cpu_sample_s / max(1, args.steps))
+    import oracle as O
+    t0 = time.perf_counter()
+    H = O.HTLR(w.d, w.n, w.ktype, w.leaf, w.p, w.eta, a=w.a(), scale=w.kscale, param=w.kparam)
+    t_con = time.perf_counter() - t0
+    u = w.u(nrhs=1)
+    for _ in range(args.warmup):
+        H.matvec(u)
+    times = []
+    for _ in range(args.steps):
+        t1 = time.perf_counter()
+        H.matvec(u)
+        times.append(time.perf_counter() - t1)
+    H.free()
+    t = statistics.mean(times)
+    val = w.N / t / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": workload_desc(w, "oracle (per-block)")},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"construct {t_con:.1f} s once, then {args.steps} HMultVec "
+                                   f"calls (single thread) on the full workload"},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------------
+def algorithmic_stream_bytes(info, w):
+    """Bytes the stream kernel must read per launch: every admissible block's core
+    (p_eff^d x p_eff^d doubles) and every inadmissible block (|tau| x |sigma| doubles)."""
+    d = w.d
+    total = 0.0
+    for lv, nfar in enumerate(info["far_per_level"]):
+        if nfar == 0:
+            continue
+        nb = w.n >> lv
+        pe = min(w.p, nb)
+        total += nfar * (pe ** d) ** 2 * 8.0
+    rows = w.leaf ** d
+    total += info["near_blocks"] * rows * rows * 8.0
+    return total
+
+
+def run_gpu(args, w):
+    import torch
+    from paper_2508_05958_gb300 import htlr
+    rank, world, local = dist_env()
+    dev = local if torch.cuda.device_count() > local else 0
+    torch.cuda.set_device(dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", dev))
+    stream = torch.cuda.Stream()
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    fp64_peak_tflops = 1.25   # nominal GB300 FP64 rate (recipe table)
+
+    t0 = time.perf_counter()
+    H = htlr.htlr_construct(w.ktype, w.d, w.n, w.leaf, w.p, w.eta, kscale=w.kscale,
+                            kparam=w.kparam, a=w.a(), storage=args.storage, stream=stream)
+    torch.cuda.synchronize()
+    construct_s = time.perf_counter() - t0
+    info = htlr.htlr_info(H)
+    storage_name = {1: "STORED", 2: "SHARED"}.get(info["storage"], "?")
+    nrhs = w.nrhs
+    U = w.u(nrhs=nrhs)
+    with torch.cuda.stream(stream):
+        ud = torch.from_numpy(np.ascontiguousarray(U.T)).cuda()
+        fd = torch.empty_like(ud)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+
+    for _ in range(max(3, args.warmup)):
+        htlr.htlr_matvec(H, ud, fd, nrhs)
+    torch.cuda.synchronize()
+    launches_per_step = htlr.htlr_last_launch_count(H)
+
+    # timed region: per-step CUDA events on the handle's stream, L2 flushed between steps
+    clocks = ClockSampler(dev)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms, stage = [], np.zeros(4)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(k))                 # evicts L2 (256 MB > 129 MB)
+            ev[k][0].record(stream)
+        st = htlr.htlr_matvec_timed(H, ud, fd, nrhs)   # events around each stage, same stream
+        with torch.cuda.stream(stream):
+            ev[k][1].record(stream)
+        stage += np.array(st)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = float(np.mean(step_ms))
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * w.N * nrhs / (ms * 1e-3) / 1e9
+    stage_ms = stage / args.steps
+
+    # roofline of the dominant kernel (the block stream)
+    alg_bytes = algorithmic_stream_bytes(info, w)
+    stream_ms = stage_ms[1]
+    achieved_gbs = alg_bytes / (stream_ms * 1e-3) / 1e9
+    fp64_tflops = alg_bytes / 8.0 * 2.0 * nrhs / (stream_ms * 1e-3) / 1e12
+    # which roof binds: FP64 pipe (1 FMA per streamed double) or HBM
+    t_hbm = alg_bytes / (hbm_peak * 1e9)
+    t_fp = alg_bytes / 8.0 * 2.0 * nrhs / (fp64_peak_tflops * 1e12)
+    if t_fp > t_hbm:
+        roof = {"bound": "alu", "achieved": fp64_tflops, "peak": fp64_peak_tflops,
+                "unit": "TFLOP/s", "frac": fp64_tflops / fp64_peak_tflops,
+                "peak_source": "nominal FP64 1.25 TFLOP/s (152 SMs x 2 FP64 FMA/clk x 2.07 GHz)"}
+    else:
+        roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved_gbs / hbm_peak, "peak_source": hbm_src}
+    roof.update({"kernel": "stream_kernel", "algorithmic_bytes_per_launch": alg_bytes,
+                 "kernel_ms": stream_ms, "hbm_achieved_gbs": achieved_gbs,
+                 "hbm_frac_of_measured": achieved_gbs / hbm_peak, "traffic": None})
+
+    # end to end through the host-buffer entry point (pinned host memory, copies timed)
+    uh = torch.from_numpy(np.ascontiguousarray(U.T)).pin_memory().numpy()
+    fh = torch.empty(uh.shape, dtype=torch.float64).pin_memory().numpy()
+    for _ in range(2):
+        htlr.htlr_matvec_host(H, uh, fh, nrhs)
+    e2e_times = []
+    for _ in range(max(3, min(args.steps, 20))):
+        t1 = time.perf_counter()
+        htlr.htlr_matvec_host(H, uh, fh, nrhs)
+        e2e_times.append(time.perf_counter() - t1)
+    e2e_s = float(np.mean(e2e_times))
+    io_bytes = w.N * nrhs * 8
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_desc(w, storage_name), "l2": "flushed between steps "
+                   "(256 MB write); blocks streamed per step: %.2f GB" % (alg_bytes / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "construct_s": construct_s, "stage_ms": {"up": stage_ms[0],
+                   "stream": stage_ms[1], "reduce": stage_ms[2], "out": stage_ms[3]},
+                   "bytes_total": info["bytes_total"], "far_per_level": info["far_per_level"],
+                   "near_blocks": info["near_blocks"]},
+        "roofline": roof,
+        "e2e": {"value": w.N * nrhs / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": io_bytes,
+                "d2h_bytes_per_step": io_bytes, "entry_point": "htlr_matvec_host"},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        val, cores, sample, _ = time_oracle(w, args.cpu_sample_s)
+        line["cpu_baseline"] = {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": sample}
+    htlr.htlr_free(H)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    from paper_2508_05958_gb300.workloads import workload
+    w = workload(args.config)
+    if args.impl == "reference":
+        run_reference(args, w)
+        return
+    run_gpu(args, w)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,189 @@
+/*
+ * htlr.h -- C ABI of the GB300 (sm_103a) HTLR library.
+ *
+ * Hierarchical Tucker low-rank (HTLR) matrices, after Li & Liu, "Hierarchical Tucker
+ * Low-Rank Matrices: Construction and Matrix-Vector Multiplication" (arXiv 2508.05958).
+ * The library builds the HTLR representation of the Nystrom operator
+ *
+ *     f_i = a(x_i) u_i + sum_j K_ij w_j u_j,                      (eq. (1.3), §3.3)
+ *     K_ij = k(x_i, x_j) (j != i),  K_ii w_i = int_{Omega_i} k(x_i, y) dy   (eq. (1.4))
+ *
+ * on a tensor grid of [0,1]^d (d = 2 or 3, N = n^d points, w_j = |Omega_j| = h^d on the
+ * uniform grid of Example 2.1) and applies it to vectors (HMultVec, Algorithm 2).
+ *
+ * Conventions shared by every call:
+ *   - Points are numbered in natural order i_1 + n i_2 + n^2 i_3 (first index fastest, §2.1).
+ *   - Vectors are N x nrhs, column-major, leading dimension N, FP64.
+ *   - All calls return HTLR_OK (0) or a negative htlr_status; no C++ exception crosses the
+ *     ABI.  On failure htlr_last_error() returns a message for the calling thread.
+ *   - Device work is enqueued on the handle's CUDA stream; calls that take device
+ *     pointers return before the work finishes.
+ *   - Every call is made on the CUDA device that was current at construction.
+ */
+#ifndef HTLR_H
+#define HTLR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+typedef enum {
+    HTLR_OK = 0,
+    HTLR_EINVAL = -1,        /* invalid argument (the message names it) */
+    HTLR_ENOMEM = -2,        /* footprint above the HBM limit, checked before allocating */
+    HTLR_ECUDA = -3,         /* a CUDA runtime call failed (message has the CUDA error) */
+    HTLR_EUNSUPPORTED = -4,  /* valid, but not supported by this build (e.g. SHARED storage
+                                on a non translation-invariant setting) */
+    HTLR_ETIMEOUT = -5,      /* a bounded device wait ran out */
+    HTLR_EDEVICE = -6        /* a kernel reported an internal check failure */
+} htlr_status;
+
+/* Kernel functions k(x, y), r = |x - y|.  The paper's experiments use the Gaussian and the
+ * single-layer potential (§5): SLP is LOG with scale -1/(2 pi) in 2D and INV_R with scale
+ * 1/(4 pi) in 3D. */
+typedef enum {
+    HTLR_K_LOG = 0,    /* scale * log r */
+    HTLR_K_INV_R = 1,  /* scale / r */
+    HTLR_K_EXP_R = 2,  /* scale * exp(-r) */
+    HTLR_K_GAUSS = 3,  /* scale * exp(-r^2 / (2 param^2)), param = sigma */
+    HTLR_K_POLY = 4,   /* scale * prod_l (x_l - y_l + 2 + l/2)^param, l = 0..d-1: a test
+                          kernel of per-dimension degree param (integer 0..16) */
+    HTLR_K_CONST = 5   /* scale */
+} htlr_kernel_type;
+
+typedef struct {
+    int type;        /* htlr_kernel_type */
+    double scale;
+    double param;
+} htlr_kernel;
+
+typedef enum {
+    HTLR_GRID_UNIFORM = 0,  /* x_i = (i + 1/2)/n, cells [i/n, (i+1)/n] (Example 2.1) */
+    HTLR_GRID_TENSOR = 1    /* per-dimension coordinates and cell edges given (§3.3) */
+} htlr_grid_type;
+
+typedef struct {
+    int type;              /* htlr_grid_type */
+    const double *coords;  /* TENSOR: d*n host doubles, coords[l*n + i], increasing in (0,1) */
+    const double *edges;   /* TENSOR: d*(n+1) host doubles, cell of line i in dimension l is
+                              [edges[l*(n+1)+i], edges[l*(n+1)+i+1]], edges 0 and 1 at the ends */
+    const double *a;       /* host array of N values a(x_i) in natural order, or NULL: a = 0 */
+} htlr_grid;
+
+/* How admissible-block cores and inadmissible blocks are held in HBM. */
+typedef enum {
+    HTLR_STORE_AUTO = 0,    /* STORED if it fits the limit, else SHARED when allowed */
+    HTLR_STORE_STORED = 1,  /* one core per admissible block and one dense matrix per
+                               inadmissible block, as Algorithm 1 builds them */
+    HTLR_STORE_SHARED = 2   /* uniform grid + translation-invariant kernel: blocks with the
+                               same level and box offset are equal, so one core (and one
+                               dense block) per (level, offset) is kept */
+} htlr_storage;
+
+typedef struct {
+    int storage;       /* htlr_storage (default AUTO) */
+    int orth;          /* 1: QR-orthonormalise the factors (Algorithm 1), 0: keep the
+                          interpolation factors; -1: default (1) */
+    int quad_order;    /* Gauss-Legendre points per dimension and sub-box for the diagonal
+                          integral (default 16, range 1..64) */
+    void *stream;      /* cudaStream_t for construction and matvecs (NULL: default stream) */
+    size_t hbm_limit;  /* maximum bytes the handle may allocate (0: 90% of free memory) */
+} htlr_options;
+
+/* Statistics of a constructed operator (htlr_info). */
+#define HTLR_MAX_LEVELS 16
+typedef struct {
+    int d, n, levels;                 /* levels L: the leaves are at level L */
+    int p, p_eff_leaf;                /* Tucker rank p and its value after QR at the leaves */
+    int storage;                      /* the htlr_storage actually used */
+    int64_t far_per_level[HTLR_MAX_LEVELS];  /* admissible leaves (TLR blocks) per level */
+    int64_t near_blocks;              /* inadmissible leaves (dense blocks) */
+    int64_t unique_cores;             /* cores held (== far blocks for STORED) */
+    int64_t unique_near;              /* dense blocks held */
+    double paper_storage_doubles;     /* storage of the paper's layout: per far block p_eff^{2d}
+                                         core + factors sum_l (|tau_l| + |sigma_l|) p_eff, per
+                                         near block |tau| |sigma| (Prop. 3.4/3.5, §5) */
+    size_t bytes_cores, bytes_near, bytes_factors, bytes_work, bytes_total;
+    double diag_value;                /* K_ii w_i on the uniform grid (eq. (1.4)) */
+} htlr_stats;
+
+typedef struct htlr_handle htlr_handle;
+
+/*
+ * htlr_construct -- Construct (Algorithm 1) on the current device.
+ *   H      out: new handle; owns every device allocation it makes.
+ *   k      kernel function (copied).
+ *   d      2 or 3.
+ *   n      points per dimension; n = leaf * 2^L with L >= 1 and L < HTLR_MAX_LEVELS.
+ *   grid   grid description (copied); NULL means the uniform grid with a = 0.
+ *   leaf   points per dimension in a leaf box (the leaf test |tau| <= N_0 of §2.2 with
+ *          N_0 = leaf^d).
+ *   r      Tucker rank p: Chebyshev points per dimension (1..16).
+ *   eta    strong admissibility max(diam) <= eta * dist (Def. 2.3) on the geometric tree
+ *          cells; eta <= 0 selects weak admissibility (Def. 2.2).
+ * Errors: HTLR_EINVAL (bad argument), HTLR_ENOMEM (footprint over the limit, nothing
+ * allocated), HTLR_EUNSUPPORTED, HTLR_ECUDA.  *H is NULL on failure.
+ * Synchronous: returns after the construction kernels finished.
+ */
+int htlr_construct(htlr_handle **H, const htlr_kernel *k, int d, int n,
+                   const htlr_grid *grid, int leaf, int r, double eta);
+
+/* htlr_construct with options (o may be NULL for defaults). */
+int htlr_construct_ex(htlr_handle **H, const htlr_kernel *k, int d, int n,
+                      const htlr_grid *grid, int leaf, int r, double eta,
+                      const htlr_options *o);
+
+/*
+ * htlr_matvec -- f = A u (HMultVec, Algorithm 2, started from the root with f = 0).
+ *   u, f   device pointers, N x nrhs column-major FP64, caller-owned; must not overlap.
+ *   nrhs   >= 1.
+ * Asynchronous on the handle's stream.  f is overwritten.
+ */
+int htlr_matvec(const htlr_handle *H, const double *u, double *f, int nrhs);
+
+/*
+ * htlr_matvec_host -- f = A u with HOST arrays: copies u to the device, applies, copies f
+ * back, all on the handle's stream, and returns after f is in host memory.  Uses device
+ * staging buffers owned by the handle (grown on demand).
+ */
+int htlr_matvec_host(htlr_handle *H, const double *u_host, double *f_host, int nrhs);
+
+/*
+ * htlr_matvec_timed -- htlr_matvec that also measures, with CUDA events recorded on the
+ * handle's stream, the device time of each stage: stage_ms[0] upward contractions,
+ * [1] block streaming (cores and dense blocks), [2] per-row reductions, [3] downward
+ * expansion + output.  Times are summed over RHS chunks.  Synchronous (waits for the
+ * stream).  stage_ms: host array of HTLR_NUM_STAGES floats.
+ */
+#define HTLR_NUM_STAGES 4
+int htlr_matvec_timed(const htlr_handle *H, const double *u, double *f, int nrhs,
+                      float *stage_ms);
+
+/* Release everything the handle owns.  NULL is a no-op.  A second free of the same
+ * handle is detected through a magic word and ignored (reported by htlr_last_error). */
+void htlr_free(htlr_handle *H);
+
+/* Fill *s with the structure and memory statistics. */
+int htlr_info(const htlr_handle *H, htlr_stats *s);
+
+/* Replace the stream used by later calls on H (NULL: default stream). */
+int htlr_set_stream(htlr_handle *H, void *stream);
+
+/* Wait for the handle's stream and report any device-side check failure (HTLR_EDEVICE). */
+int htlr_sync(const htlr_handle *H);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *htlr_last_error(void);
+
+/* Number of kernel launches the last htlr_matvec on H enqueued. */
+int htlr_last_launch_count(const htlr_handle *H);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HTLR_H */

@@ -1,0 +1,838 @@
+// C ABI of the HTLR library: argument checks, Construct (Algorithm 1) orchestration and
+// HMultVec (Algorithm 2) orchestration.  Every step of the computation runs in the
+// kernels of plan.cu, construct.cu and apply.cu; this file only plans, allocates and
+// launches.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <set>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "htlr_internal.h"
+
+namespace htlr {
+
+static thread_local std::string g_err;
+static std::mutex g_live_mu;
+static std::set<const htlr_handle *> g_live;
+
+void set_error(const std::string &msg) { g_err = msg; }
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return HTLR_ECUDA;
+}
+
+#define HTLR_CK(call)                                   \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+static int fail(int code, const std::string &msg)
+{
+    set_error(msg);
+    return code;
+}
+
+template <class T>
+static int dalloc(htlr_handle *H, T **p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    H->allocs.push_back(q);
+    *p = static_cast<T *>(q);
+    return HTLR_OK;
+}
+
+// Scratch allocations released at the end of construction.
+struct Temps {
+    std::vector<void *> p;
+    ~Temps()
+    {
+        for (void *q : p) cudaFree(q);
+    }
+    template <class T>
+    int alloc(T **out, size_t count)
+    {
+        *out = nullptr;
+        if (count == 0) count = 1;
+        void *q = nullptr;
+        cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (temporary)");
+        p.push_back(q);
+        *out = static_cast<T *>(q);
+        return HTLR_OK;
+    }
+};
+
+// Gauss-Legendre nodes and weights on [-1, 1]: Newton's method on P_q from Tricomi's
+// asymptotic initial guesses; P_q' from the derivative recurrence
+// P'_{j+1} = P'_{j-1} + (2j + 1) P_j.
+static void gauss_legendre_host(int q, std::vector<double> &x, std::vector<double> &w)
+{
+    const double pi = 3.141592653589793238462643;
+    x.assign(q, 0.0);
+    w.assign(q, 0.0);
+    for (int k = 1; k <= q; ++k) {
+        double th = pi * (4.0 * k - 1.0) / (4.0 * q + 2.0);
+        double z = (1.0 - (q - 1.0) / (8.0 * q * q * q)) * std::cos(th);
+        double dp = 1.0;
+        for (int it = 0; it < 64; ++it) {
+            double pm1 = 1.0, p0 = z, dm1 = 0.0, d0 = 1.0;
+            for (int j = 1; j < q; ++j) {
+                double p1 = ((2.0 * j + 1.0) * z * p0 - j * pm1) / (j + 1.0);
+                double d1 = dm1 + (2.0 * j + 1.0) * p0;
+                pm1 = p0;
+                p0 = p1;
+                dm1 = d0;
+                d0 = d1;
+            }
+            dp = d0;
+            double step = p0 / d0;
+            z -= step;
+            if (std::fabs(step) <= 1e-17) break;
+        }
+        x[k - 1] = z;
+        w[k - 1] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+static int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+static int ipow(int b, int e)
+{
+    int r = 1;
+    for (int i = 0; i < e; ++i) r *= b;
+    return r;
+}
+
+// Decode a lexicographic box index of a level into its multi-index.
+static void box_index(int box, int d, int level, int *b)
+{
+    int m = (1 << level) - 1;
+    for (int k = 0; k < d; ++k) b[k] = (box >> (level * k)) & m;
+    for (int k = d; k < 3; ++k) b[k] = 0;
+}
+
+struct Sizes {
+    size_t cores = 0, near = 0, factors = 0, work = 0, lists = 0;
+    size_t total() const { return cores + near + factors + work + lists; }
+};
+
+static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
+{
+    const int d = H->d, n = H->n, leaf = H->leaf, p = H->p, L = H->L;
+    const long long N = (long long)ipow(n, d);
+    cudaStream_t s = H->stream;
+    H->h = 1.0 / n;
+    H->wgt = std::pow(H->h, d);
+    Temps tmp;
+
+    if (dalloc(H, &H->d_err, 1)) return HTLR_ECUDA;
+    HTLR_CK(cudaMemsetAsync(H->d_err, 0, sizeof(int), s));
+    if (grid && grid->a) {
+        if (dalloc(H, &H->d_a, (size_t)N)) return HTLR_ECUDA;
+        HTLR_CK(cudaMemcpyAsync(H->d_a, grid->a, sizeof(double) * N, cudaMemcpyHostToDevice, s));
+    }
+
+    // ---- Nystrom diagonal (eq. (1.4)) ----
+    {
+        std::vector<double> gx, gw;
+        gauss_legendre_host(H->q, gx, gw);
+        double *d_g = nullptr;
+        if (tmp.alloc(&d_g, 2 * H->q + 1)) return HTLR_ECUDA;
+        HTLR_CK(cudaMemcpyAsync(d_g, gx.data(), sizeof(double) * H->q, cudaMemcpyHostToDevice, s));
+        HTLR_CK(cudaMemcpyAsync(d_g + H->q, gw.data(), sizeof(double) * H->q,
+                                cudaMemcpyHostToDevice, s));
+        launch_diag(H->kern, d, H->h, H->q, d_g, d_g + H->q, d_g + 2 * H->q, s);
+        HTLR_CK(cudaGetLastError());
+        HTLR_CK(cudaMemcpyAsync(&H->diag, d_g + 2 * H->q, sizeof(double), cudaMemcpyDeviceToHost, s));
+        HTLR_CK(cudaStreamSynchronize(s));
+    }
+
+    // ---- block cluster tree walk (Def. 2.4), level by level ----
+    H->lev.assign(L + 1, LevelData());
+    std::vector<int> prev_rowptr = {0, 1}, prev_col = {0};
+    for (int lv = 1; lv <= L; ++lv) {
+        LevelData &Lv = H->lev[lv];
+        Lv.level = lv;
+        Lv.nbox1 = 1 << lv;
+        Lv.nbox = 1 << (d * lv);
+        Lv.nb = n >> lv;
+        const int nbox = Lv.nbox;
+        int *d_prow, *d_pcol, *d_cnt, *d_off, *d_fcol, *d_ncol;
+        if (tmp.alloc(&d_prow, prev_rowptr.size()) || tmp.alloc(&d_pcol, prev_col.size()) ||
+            tmp.alloc(&d_cnt, 2 * (size_t)nbox) || tmp.alloc(&d_off, 2 * (size_t)nbox))
+            return HTLR_ECUDA;
+        HTLR_CK(cudaMemcpyAsync(d_prow, prev_rowptr.data(), sizeof(int) * prev_rowptr.size(),
+                                cudaMemcpyHostToDevice, s));
+        HTLR_CK(cudaMemcpyAsync(d_pcol, prev_col.data(), sizeof(int) * prev_col.size(),
+                                cudaMemcpyHostToDevice, s));
+        launch_walk(0, d, lv, H->eta, d_prow, d_pcol, d_cnt, d_cnt + nbox, nullptr, nullptr,
+                    nullptr, nullptr, s);
+        HTLR_CK(cudaGetLastError());
+        std::vector<int> cnt(2 * (size_t)nbox);
+        HTLR_CK(cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(int) * cnt.size(), cudaMemcpyDeviceToHost, s));
+        HTLR_CK(cudaStreamSynchronize(s));
+        std::vector<int> off(2 * (size_t)nbox);
+        Lv.far_rowptr.assign(nbox + 1, 0);
+        std::vector<int> near_rowptr(nbox + 1, 0);
+        for (int t = 0; t < nbox; ++t) {
+            Lv.far_rowptr[t + 1] = Lv.far_rowptr[t] + cnt[t];
+            near_rowptr[t + 1] = near_rowptr[t] + cnt[nbox + t];
+            off[t] = Lv.far_rowptr[t];
+            off[nbox + t] = near_rowptr[t];
+        }
+        Lv.nfar = Lv.far_rowptr[nbox];
+        long long nnear = near_rowptr[nbox];
+        if (tmp.alloc(&d_fcol, Lv.nfar) || tmp.alloc(&d_ncol, nnear)) return HTLR_ECUDA;
+        HTLR_CK(cudaMemcpyAsync(d_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice, s));
+        launch_walk(1, d, lv, H->eta, d_prow, d_pcol, nullptr, nullptr, d_off, d_off + nbox,
+                    d_fcol, d_ncol, s);
+        HTLR_CK(cudaGetLastError());
+        Lv.far_col.resize(Lv.nfar);
+        std::vector<int> near_col(nnear);
+        if (Lv.nfar)
+            HTLR_CK(cudaMemcpyAsync(Lv.far_col.data(), d_fcol, sizeof(int) * Lv.nfar,
+                                    cudaMemcpyDeviceToHost, s));
+        if (nnear)
+            HTLR_CK(cudaMemcpyAsync(near_col.data(), d_ncol, sizeof(int) * nnear,
+                                    cudaMemcpyDeviceToHost, s));
+        HTLR_CK(cudaStreamSynchronize(s));
+        prev_rowptr.swap(near_rowptr);
+        prev_col.swap(near_col);
+    }
+    H->near_rowptr = prev_rowptr;
+    H->near_col = prev_col;
+    H->nnear = (int64_t)H->near_col.size();
+
+    // ---- per-level shapes and the storage decision ----
+    const int rows_leaf = ipow(leaf, d);
+    H->near_rows = rows_leaf;
+    H->near_ld = round_up(rows_leaf, 32);
+    if (H->near_ld / 32 > 16)
+        return fail(HTLR_EUNSUPPORTED, "leaf boxes above 512 points are not supported");
+    int first_far = -1;
+    for (int lv = 1; lv <= L; ++lv) {
+        LevelData &Lv = H->lev[lv];
+        if (Lv.nfar == 0) continue;
+        if (first_far < 0) first_far = lv;
+        Lv.pe = H->orth ? std::min(p, Lv.nb) : p;
+        Lv.pd = ipow(Lv.pe, d);
+        Lv.ld = round_up(Lv.pd, 32);
+        if (Lv.ld / 32 > 16)
+            return fail(HTLR_EUNSUPPORTED, "p_eff^d above 512 is not supported");
+    }
+
+    // unique offsets (tau - sigma) per level and for the inadmissible leaves
+    auto offset_key = [&](int tau, int sig, int level) {
+        int bt[3], bs[3];
+        box_index(tau, d, level, bt);
+        box_index(sig, d, level, bs);
+        return std::make_tuple(bt[0] - bs[0], bt[1] - bs[1], bt[2] - bs[2]);
+    };
+    std::vector<std::vector<int>> shared_id(L + 1);
+    std::vector<std::vector<std::tuple<int, int, int>>> shared_off(L + 1);
+    for (int lv = 1; lv <= L; ++lv) {
+        LevelData &Lv = H->lev[lv];
+        if (Lv.nfar == 0) continue;
+        std::map<std::tuple<int, int, int>, int> ids;
+        shared_id[lv].resize(Lv.nfar);
+        for (int t = 0; t < Lv.nbox; ++t)
+            for (int e = Lv.far_rowptr[t]; e < Lv.far_rowptr[t + 1]; ++e) {
+                auto key = offset_key(t, Lv.far_col[e], lv);
+                auto it = ids.find(key);
+                int id;
+                if (it == ids.end()) {
+                    id = (int)shared_off[lv].size();
+                    ids[key] = id;
+                    shared_off[lv].push_back(key);
+                } else {
+                    id = it->second;
+                }
+                shared_id[lv][e] = id;
+            }
+    }
+    std::vector<int> near_shared_id(H->nnear);
+    std::vector<std::tuple<int, int, int>> near_shared_off;
+    {
+        std::map<std::tuple<int, int, int>, int> ids;
+        const int nleaf = 1 << (d * L);
+        for (int t = 0; t < nleaf; ++t)
+            for (int e = H->near_rowptr[t]; e < H->near_rowptr[t + 1]; ++e) {
+                auto key = offset_key(t, H->near_col[e], L);
+                auto it = ids.find(key);
+                int id;
+                if (it == ids.end()) {
+                    id = (int)near_shared_off.size();
+                    ids[key] = id;
+                    near_shared_off.push_back(key);
+                } else {
+                    id = it->second;
+                }
+                near_shared_id[e] = id;
+            }
+    }
+
+    // tasks: runs of consecutive entries of one row, about kTaskBytes of blocks each
+    const size_t kTaskBytes = 256 * 1024;
+    H->nrc = 4;
+    auto count_tasks = [&](const std::vector<int> &rowptr, int nrows, size_t blk_bytes) {
+        long long per = std::max<long long>(1, (long long)(kTaskBytes / blk_bytes));
+        long long nt = 0;
+        for (int t = 0; t < nrows; ++t) {
+            long long m = rowptr[t + 1] - rowptr[t];
+            nt += (m + per - 1) / per;
+        }
+        return std::make_pair(nt, per);
+    };
+    Sizes sz_stored, sz_shared;
+    long long part_doubles = 0, ntasks = 0;
+    for (int lv = 1; lv <= L; ++lv) {
+        LevelData &Lv = H->lev[lv];
+        if (Lv.nfar == 0) continue;
+        size_t blk = (size_t)Lv.ld * Lv.pd * sizeof(double);
+        auto ct = count_tasks(Lv.far_rowptr, Lv.nbox, blk);
+        ntasks += ct.first;
+        part_doubles += ct.first * (long long)H->nrc * Lv.ld;
+        sz_stored.cores += blk * Lv.nfar;
+        sz_shared.cores += blk * shared_off[lv].size();
+        size_t fac = sizeof(double) * (2 * (size_t)Lv.nb * p + (size_t)p * p);
+        size_t work = 2 * sizeof(double) * (size_t)Lv.nbox * H->nrc * Lv.pd;
+        size_t lists = sizeof(int) * (2 * (size_t)Lv.nfar + 2 * ((size_t)Lv.nbox + 1));
+        for (Sizes *z : {&sz_stored, &sz_shared}) {
+            z->factors += fac;
+            z->work += work;
+            z->lists += lists;
+        }
+    }
+    {
+        size_t blk = (size_t)H->near_ld * rows_leaf * sizeof(double);
+        auto ct = count_tasks(H->near_rowptr, 1 << (d * L), blk);
+        ntasks += ct.first;
+        part_doubles += ct.first * (long long)H->nrc * H->near_ld;
+        sz_stored.near = blk * H->nnear;
+        sz_shared.near = blk * near_shared_off.size();
+        size_t lists = sizeof(int) * (2 * (size_t)H->nnear + 2 * ((size_t)(1 << (d * L)) + 1));
+        size_t work = sizeof(double) * part_doubles + sizeof(Task) * ntasks;
+        for (Sizes *z : {&sz_stored, &sz_shared}) {
+            z->lists += lists;
+            z->work += work;
+        }
+    }
+    size_t limit = o ? o->hbm_limit : 0;
+    if (limit == 0) {
+        size_t fr = 0, tot = 0;
+        HTLR_CK(cudaMemGetInfo(&fr, &tot));
+        limit = (size_t)(0.9 * (double)fr);
+    }
+    int want = o ? o->storage : HTLR_STORE_AUTO;
+    if (want == HTLR_STORE_AUTO) want = sz_stored.total() <= limit ? HTLR_STORE_STORED : HTLR_STORE_SHARED;
+    if (want != HTLR_STORE_STORED && want != HTLR_STORE_SHARED)
+        return fail(HTLR_EINVAL, "options.storage must be AUTO, STORED or SHARED");
+    const Sizes &sz = (want == HTLR_STORE_STORED) ? sz_stored : sz_shared;
+    if (sz.total() > limit) {
+        char buf[256];
+        snprintf(buf, sizeof buf, "footprint %.3f GB exceeds the limit %.3f GB (storage %s)",
+                 sz.total() / 1e9, limit / 1e9, want == HTLR_STORE_STORED ? "STORED" : "SHARED");
+        return fail(HTLR_ENOMEM, buf);
+    }
+    H->storage = want;
+    const bool stored = (want == HTLR_STORE_STORED);
+
+    // ---- factors, cores, dense blocks (Algorithm 1) ----
+    long long pdf = ipow(p, d);
+    long long scratch_per = 2 * pdf * pdf;
+    int nscr = (int)std::max<long long>(1, std::min<long long>(2 * 152, (512ll << 20) / (8 * scratch_per)));
+    double *d_scratch = nullptr;
+    if (first_far >= 0 && tmp.alloc(&d_scratch, (size_t)nscr * scratch_per)) return HTLR_ECUDA;
+    for (int lv = 1; lv <= L; ++lv) {
+        LevelData &Lv = H->lev[lv];
+        if (Lv.nfar == 0) continue;
+        if (dalloc(H, &Lv.d_F, 2 * (size_t)Lv.nb * p) || dalloc(H, &Lv.d_R, (size_t)p * p))
+            return HTLR_ECUDA;
+        double side = std::ldexp(1.0, -lv);
+        launch_factor(Lv.nb, p, Lv.pe, side, H->h, H->orth, Lv.d_F, Lv.d_R, s);
+        HTLR_CK(cudaGetLastError());
+        // core per block (STORED) or per offset (SHARED)
+        std::vector<int> offs;
+        if (stored) {
+            Lv.far_core.resize(Lv.nfar);
+            offs.resize(3 * (size_t)Lv.nfar);
+            for (int t = 0; t < Lv.nbox; ++t)
+                for (int e = Lv.far_rowptr[t]; e < Lv.far_rowptr[t + 1]; ++e) {
+                    auto key = offset_key(t, Lv.far_col[e], lv);
+                    offs[3 * (size_t)e] = std::get<0>(key);
+                    offs[3 * (size_t)e + 1] = std::get<1>(key);
+                    offs[3 * (size_t)e + 2] = std::get<2>(key);
+                    Lv.far_core[e] = e;
+                }
+            Lv.ncores = Lv.nfar;
+        } else {
+            Lv.far_core = shared_id[lv];
+            Lv.ncores = (int64_t)shared_off[lv].size();
+            offs.resize(3 * (size_t)Lv.ncores);
+            for (size_t c = 0; c < shared_off[lv].size(); ++c) {
+                offs[3 * c] = std::get<0>(shared_off[lv][c]);
+                offs[3 * c + 1] = std::get<1>(shared_off[lv][c]);
+                offs[3 * c + 2] = std::get<2>(shared_off[lv][c]);
+            }
+        }
+        int *d_offs = nullptr;
+        if (tmp.alloc(&d_offs, offs.size())) return HTLR_ECUDA;
+        HTLR_CK(cudaMemcpyAsync(d_offs, offs.data(), sizeof(int) * offs.size(), cudaMemcpyHostToDevice, s));
+        if (dalloc(H, &Lv.d_cores, (size_t)Lv.ncores * Lv.ld * Lv.pd)) return HTLR_ECUDA;
+        launch_cores(H->kern, d, p, Lv.pe, Lv.ld, H->orth, side, H->wgt, Lv.d_R, Lv.ncores, d_offs,
+                     Lv.d_cores, d_scratch, nscr, s);
+        HTLR_CK(cudaGetLastError());
+        // lists
+        if (dalloc(H, &Lv.d_far_col, Lv.nfar) || dalloc(H, &Lv.d_far_core, Lv.nfar) ||
+            dalloc(H, &Lv.d_W, (size_t)Lv.nbox * H->nrc * Lv.pd) ||
+            dalloc(H, &Lv.d_H, (size_t)Lv.nbox * H->nrc * Lv.pd))
+            return HTLR_ECUDA;
+        HTLR_CK(cudaMemcpyAsync(Lv.d_far_col, Lv.far_col.data(), sizeof(int) * Lv.nfar,
+                                cudaMemcpyHostToDevice, s));
+        HTLR_CK(cudaMemcpyAsync(Lv.d_far_core, Lv.far_core.data(), sizeof(int) * Lv.nfar,
+                                cudaMemcpyHostToDevice, s));
+        HTLR_CK(cudaStreamSynchronize(s));  // offs / far_core host buffers go out of scope
+    }
+    // dense inadmissible leaves
+    {
+        std::vector<int> offs, taus;
+        if (stored) {
+            H->near_blk.resize(H->nnear);
+            offs.resize(3 * (size_t)H->nnear);
+            taus.resize(H->nnear);
+            const int nleaf = 1 << (d * L);
+            for (int t = 0; t < nleaf; ++t)
+                for (int e = H->near_rowptr[t]; e < H->near_rowptr[t + 1]; ++e) {
+                    auto key = offset_key(t, H->near_col[e], L);
+                    offs[3 * (size_t)e] = std::get<0>(key);
+                    offs[3 * (size_t)e + 1] = std::get<1>(key);
+                    offs[3 * (size_t)e + 2] = std::get<2>(key);
+                    taus[e] = t;
+                    H->near_blk[e] = e;
+                }
+            H->nnear_unique = H->nnear;
+        } else {
+            H->near_blk = near_shared_id;
+            H->nnear_unique = (int64_t)near_shared_off.size();
+            offs.resize(3 * (size_t)H->nnear_unique);
+            for (size_t c = 0; c < near_shared_off.size(); ++c) {
+                offs[3 * c] = std::get<0>(near_shared_off[c]);
+                offs[3 * c + 1] = std::get<1>(near_shared_off[c]);
+                offs[3 * c + 2] = std::get<2>(near_shared_off[c]);
+            }
+        }
+        int *d_offs = nullptr, *d_taus = nullptr;
+        if (tmp.alloc(&d_offs, offs.size()) || tmp.alloc(&d_taus, taus.size())) return HTLR_ECUDA;
+        HTLR_CK(cudaMemcpyAsync(d_offs, offs.data(), sizeof(int) * offs.size(), cudaMemcpyHostToDevice, s));
+        if (!taus.empty())
+            HTLR_CK(cudaMemcpyAsync(d_taus, taus.data(), sizeof(int) * taus.size(),
+                                    cudaMemcpyHostToDevice, s));
+        if (dalloc(H, &H->d_near, (size_t)H->nnear_unique * H->near_ld * rows_leaf) ||
+            dalloc(H, &H->d_near_col, H->nnear) || dalloc(H, &H->d_near_blk, H->nnear))
+            return HTLR_ECUDA;
+        launch_near(H->kern, d, n, leaf, H->near_ld, H->h, H->wgt, H->diag,
+                    stored ? H->d_a : nullptr, H->nnear_unique, d_offs, stored ? d_taus : nullptr,
+                    H->d_near, s);
+        HTLR_CK(cudaGetLastError());
+        HTLR_CK(cudaMemcpyAsync(H->d_near_col, H->near_col.data(), sizeof(int) * H->nnear,
+                                cudaMemcpyHostToDevice, s));
+        HTLR_CK(cudaMemcpyAsync(H->d_near_blk, H->near_blk.data(), sizeof(int) * H->nnear,
+                                cudaMemcpyHostToDevice, s));
+        HTLR_CK(cudaStreamSynchronize(s));
+    }
+
+    // ---- task list and kinds ----
+    H->kinds.assign(L + 2, KindDesc{});
+    H->tasks.clear();
+    long long part = 0;
+    auto make_tasks = [&](int kind, const std::vector<int> &rowptr, int nrows, size_t blk_bytes,
+                          int ld, std::vector<int> &row_task) {
+        long long per = std::max<long long>(1, (long long)(kTaskBytes / blk_bytes));
+        row_task.assign(nrows + 1, 0);
+        for (int t = 0; t < nrows; ++t) {
+            row_task[t] = (int)H->tasks.size();
+            for (long long e = rowptr[t]; e < rowptr[t + 1]; e += per) {
+                Task T;
+                T.kind = kind;
+                T.row = t;
+                T.e0 = (int)e;
+                T.e1 = (int)std::min<long long>(rowptr[t + 1], e + per);
+                T.part = part;
+                part += (long long)H->nrc * ld;
+                H->tasks.push_back(T);
+            }
+        }
+        row_task[nrows] = (int)H->tasks.size();
+    };
+    int max_cols = 1;
+    for (int lv = 1; lv <= L; ++lv) {
+        LevelData &Lv = H->lev[lv];
+        if (Lv.nfar == 0) continue;
+        make_tasks(lv, Lv.far_rowptr, Lv.nbox, (size_t)Lv.ld * Lv.pd * sizeof(double), Lv.ld,
+                   Lv.row_task_begin);
+        KindDesc &K = H->kinds[lv];
+        K.col = Lv.d_far_col;
+        K.blk = Lv.d_far_core;
+        K.blocks = Lv.d_cores;
+        K.blk_stride = (long long)Lv.ld * Lv.pd;
+        K.ld = Lv.ld;
+        K.rows = Lv.pd;
+        K.cols = Lv.pd;
+        K.rpl = Lv.ld / 32;
+        K.is_near = 0;
+        K.x = Lv.d_W;
+        K.x_box_stride = (long long)H->nrc * Lv.pd;
+        max_cols = std::max(max_cols, Lv.pd);
+        if (dalloc(H, &Lv.d_row_task, Lv.row_task_begin.size())) return HTLR_ECUDA;
+        HTLR_CK(cudaMemcpyAsync(Lv.d_row_task, Lv.row_task_begin.data(),
+                                sizeof(int) * Lv.row_task_begin.size(), cudaMemcpyHostToDevice, s));
+    }
+    {
+        make_tasks(L + 1, H->near_rowptr, 1 << (d * L),
+                   (size_t)H->near_ld * rows_leaf * sizeof(double), H->near_ld, H->near_row_task);
+        KindDesc &K = H->kinds[L + 1];
+        K.col = H->d_near_col;
+        K.blk = H->d_near_blk;
+        K.blocks = H->d_near;
+        K.blk_stride = (long long)H->near_ld * rows_leaf;
+        K.ld = H->near_ld;
+        K.rows = rows_leaf;
+        K.cols = rows_leaf;
+        K.rpl = H->near_ld / 32;
+        K.is_near = 1;
+        K.x = nullptr;
+        K.x_box_stride = 0;
+        max_cols = std::max(max_cols, rows_leaf);
+        if (dalloc(H, &H->d_near_row_task, H->near_row_task.size())) return HTLR_ECUDA;
+        HTLR_CK(cudaMemcpyAsync(H->d_near_row_task, H->near_row_task.data(),
+                                sizeof(int) * H->near_row_task.size(), cudaMemcpyHostToDevice, s));
+    }
+    H->part_doubles = part;
+    H->max_cols = max_cols;
+    if (dalloc(H, &H->d_part, (size_t)part) || dalloc(H, &H->d_tasks, H->tasks.size()) ||
+        dalloc(H, &H->d_kinds, H->kinds.size()))
+        return HTLR_ECUDA;
+    HTLR_CK(cudaMemcpyAsync(H->d_tasks, H->tasks.data(), sizeof(Task) * H->tasks.size(),
+                            cudaMemcpyHostToDevice, s));
+    HTLR_CK(cudaMemcpyAsync(H->d_kinds, H->kinds.data(), sizeof(KindDesc) * H->kinds.size(),
+                            cudaMemcpyHostToDevice, s));
+    HTLR_CK(cudaStreamSynchronize(s));
+
+    // ---- statistics ----
+    htlr_stats &st = H->stats;
+    std::memset(&st, 0, sizeof st);
+    st.d = d;
+    st.n = n;
+    st.levels = L;
+    st.p = p;
+    st.storage = H->storage;
+    st.p_eff_leaf = H->orth ? std::min(p, leaf) : p;
+    double paper = 0.0;
+    for (int lv = 1; lv <= L; ++lv) {
+        const LevelData &Lv = H->lev[lv];
+        st.far_per_level[lv] = Lv.nfar;
+        st.unique_cores += Lv.ncores;
+        int pe = std::min(p, Lv.nb);
+        paper += (double)Lv.nfar * (std::pow((double)pe, 2 * d) + 2.0 * d * Lv.nb * pe);
+    }
+    paper += (double)H->nnear * rows_leaf * (double)rows_leaf;
+    st.near_blocks = H->nnear;
+    st.unique_near = H->nnear_unique;
+    st.paper_storage_doubles = paper;
+    st.bytes_cores = sz.cores;
+    st.bytes_near = sz.near;
+    st.bytes_factors = sz.factors;
+    st.bytes_work = sz.work + sz.lists;
+    st.bytes_total = sz.total();
+    st.diag_value = H->diag;
+    return HTLR_OK;
+}
+
+static void destroy(htlr_handle *H)
+{
+    if (!H) return;
+    for (void *q : H->allocs) cudaFree(q);
+    if (H->d_stage_u) cudaFree(H->d_stage_u);
+    if (H->d_stage_f) cudaFree(H->d_stage_f);
+    H->allocs.clear();
+    H->magic = kMagicDead;
+    delete H;
+}
+
+static bool is_live(const htlr_handle *H)
+{
+    std::lock_guard<std::mutex> g(g_live_mu);
+    return H && g_live.count(H) && H->magic == kMagicLive;
+}
+
+// Events bracketing the stages of one matvec (optional).
+struct StageEvents {
+    cudaEvent_t ev[2 * HTLR_NUM_STAGES];
+    float ms[HTLR_NUM_STAGES];
+};
+
+static int enqueue_matvec(const htlr_handle *H, const double *u, double *f, int nrhs,
+                          StageEvents *tev = nullptr)
+{
+    const int d = H->d, n = H->n, L = H->L;
+    const long long N = (long long)ipow(n, d);
+    cudaStream_t s = H->stream;
+    int launches = 0;
+    std::vector<DownLevel> down;
+    for (int lv = 1; lv <= L; ++lv) {
+        const LevelData &Lv = H->lev[lv];
+        if (Lv.nfar == 0) continue;
+        down.push_back(DownLevel{lv, Lv.nb, Lv.pe, Lv.pd, Lv.d_F, Lv.d_H});
+    }
+    for (int c0 = 0; c0 < nrhs; c0 += H->nrc) {
+        const int nh = std::min(H->nrc, nrhs - c0);
+        const double *uc = u + (long long)c0 * N;
+        double *fc = f + (long long)c0 * N;
+        auto mark = [&](int k) {
+            if (tev) cudaEventRecord(tev->ev[k], s);
+        };
+        auto close_stage = [&](int st) {
+            if (!tev) return;
+            cudaEventSynchronize(tev->ev[2 * st + 1]);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, tev->ev[2 * st], tev->ev[2 * st + 1]);
+            tev->ms[st] += ms;
+        };
+        mark(0);
+        for (int lv = 1; lv <= L; ++lv) {
+            const LevelData &Lv = H->lev[lv];
+            if (Lv.nfar == 0) continue;
+            launch_up(d, n, lv, Lv.nb, Lv.pe, Lv.d_F, uc, nh, N, H->nrc, Lv.d_W, s);
+            ++launches;
+        }
+        mark(1);
+        mark(2);
+        launch_stream(H->d_tasks, (int)H->tasks.size(), H->d_kinds, 16, d, n, H->leaf, uc, N, nh,
+                      H->max_cols, H->d_part, H->d_err, H->storage == HTLR_STORE_STORED, s);
+        ++launches;
+        mark(3);
+        mark(4);
+        for (int lv = 1; lv <= L; ++lv) {
+            const LevelData &Lv = H->lev[lv];
+            if (Lv.nfar == 0) continue;
+            launch_reduce_far(Lv.nbox, Lv.pd, Lv.ld, H->nrc, nh, Lv.d_row_task, H->d_tasks,
+                              H->d_part, Lv.d_H, s);
+            ++launches;
+        }
+        mark(5);
+        mark(6);
+        launch_out(d, n, H->leaf, L, H->nrc, nh, H->d_near_row_task, H->d_tasks, H->d_part,
+                   H->near_ld, H->storage == HTLR_STORE_STORED ? nullptr : H->d_a, uc, N,
+                   down.data(), (int)down.size(), fc, N, s);
+        ++launches;
+        mark(7);
+        for (int st = 0; st < HTLR_NUM_STAGES; ++st) close_stage(st);
+    }
+    const_cast<htlr_handle *>(H)->last_launches = launches;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "matvec launch");
+    return HTLR_OK;
+}
+
+}  // namespace htlr
+
+using namespace htlr;
+
+extern "C" {
+
+const char *htlr_last_error(void) { return g_err.c_str(); }
+
+int htlr_construct_ex(htlr_handle **out, const htlr_kernel *k, int d, int n, const htlr_grid *grid,
+                      int leaf, int r, double eta, const htlr_options *o)
+{
+    set_error("");
+    if (!out) return fail(HTLR_EINVAL, "H must not be NULL");
+    *out = nullptr;
+    if (!k) return fail(HTLR_EINVAL, "kernel must not be NULL");
+    if (k->type < HTLR_K_LOG || k->type > HTLR_K_CONST) return fail(HTLR_EINVAL, "unknown kernel type");
+    if (!std::isfinite(k->scale) || !std::isfinite(k->param))
+        return fail(HTLR_EINVAL, "kernel scale and param must be finite");
+    if (k->type == HTLR_K_GAUSS && !(k->param > 0.0)) return fail(HTLR_EINVAL, "Gaussian sigma must be > 0");
+    if (k->type == HTLR_K_POLY && (k->param < 0 || k->param > 16 || k->param != std::floor(k->param)))
+        return fail(HTLR_EINVAL, "polynomial degree must be an integer in 0..16");
+    if (d != 2 && d != 3) return fail(HTLR_EINVAL, "d must be 2 or 3");
+    if (leaf < 1 || n < 2 || n % leaf) return fail(HTLR_EINVAL, "n must be a multiple of leaf");
+    int ratio = n / leaf, L = 0;
+    while ((1 << L) < ratio) ++L;
+    if ((1 << L) != ratio || L < 1) return fail(HTLR_EINVAL, "n / leaf must be 2^L with L >= 1");
+    if (L >= HTLR_MAX_LEVELS) return fail(HTLR_EINVAL, "too many levels");
+    if (d * L > 30) return fail(HTLR_EINVAL, "too many boxes");
+    if (r < 1 || r > kMaxP) return fail(HTLR_EINVAL, "r must be in 1..16");
+    if (!std::isfinite(eta)) return fail(HTLR_EINVAL, "eta must be finite");
+    if (grid && grid->type == HTLR_GRID_TENSOR)
+        return fail(HTLR_EUNSUPPORTED, "tensor (non-uniform) grids are not supported yet");
+    if (grid && grid->type != HTLR_GRID_UNIFORM) return fail(HTLR_EINVAL, "unknown grid type");
+    int q = (o && o->quad_order > 0) ? o->quad_order : 16;
+    if (q > 64) return fail(HTLR_EINVAL, "quad_order must be in 1..64");
+    if (o && (o->orth < -1 || o->orth > 1)) return fail(HTLR_EINVAL, "orth must be -1, 0 or 1");
+
+    htlr_handle *H = nullptr;
+    try {
+        H = new htlr_handle();
+    } catch (const std::bad_alloc &) {
+        return fail(HTLR_ENOMEM, "host allocation failed");
+    }
+    H->magic = kMagicLive;
+    cudaGetDevice(&H->device);
+    H->stream = o ? (cudaStream_t)o->stream : nullptr;
+    H->kern = KernelDesc{k->type, k->scale, k->param};
+    H->d = d;
+    H->n = n;
+    H->leaf = leaf;
+    H->p = r;
+    H->L = L;
+    H->eta = eta;
+    H->q = q;
+    H->orth = (o && o->orth == 0) ? 0 : 1;
+    int rc;
+    try {
+        rc = build(H, grid, o);
+    } catch (const std::bad_alloc &) {
+        rc = fail(HTLR_ENOMEM, "host allocation failed");
+    }
+    if (rc != HTLR_OK) {
+        std::string keep = g_err;
+        destroy(H);
+        set_error(keep);
+        return rc;
+    }
+    {
+        std::lock_guard<std::mutex> g(g_live_mu);
+        g_live.insert(H);
+    }
+    *out = H;
+    return HTLR_OK;
+}
+
+int htlr_construct(htlr_handle **out, const htlr_kernel *k, int d, int n, const htlr_grid *grid,
+                   int leaf, int r, double eta)
+{
+    return htlr_construct_ex(out, k, d, n, grid, leaf, r, eta, nullptr);
+}
+
+int htlr_matvec(const htlr_handle *H, const double *u, double *f, int nrhs)
+{
+    if (!is_live(H)) return fail(HTLR_EINVAL, "not a live HTLR handle");
+    if (!u || !f) return fail(HTLR_EINVAL, "u and f must not be NULL");
+    if (nrhs < 1) return fail(HTLR_EINVAL, "nrhs must be >= 1");
+    const long long N = (long long)ipow(H->n, H->d);
+    const char *ub = (const char *)u, *ue = (const char *)(u + N * nrhs);
+    const char *fb = (const char *)f, *fe = (const char *)(f + N * nrhs);
+    if (ub < fe && fb < ue) return fail(HTLR_EINVAL, "u and f must not overlap");
+    return enqueue_matvec(H, u, f, nrhs);
+}
+
+int htlr_matvec_timed(const htlr_handle *H, const double *u, double *f, int nrhs,
+                      float *stage_ms)
+{
+    if (!is_live(H)) return fail(HTLR_EINVAL, "not a live HTLR handle");
+    if (!u || !f || !stage_ms) return fail(HTLR_EINVAL, "u, f and stage_ms must not be NULL");
+    if (nrhs < 1) return fail(HTLR_EINVAL, "nrhs must be >= 1");
+    StageEvents tev;
+    for (int k = 0; k < 2 * HTLR_NUM_STAGES; ++k) HTLR_CK(cudaEventCreate(&tev.ev[k]));
+    for (int k = 0; k < HTLR_NUM_STAGES; ++k) tev.ms[k] = 0.f;
+    int rc = enqueue_matvec(H, u, f, nrhs, &tev);
+    cudaError_t e = cudaStreamSynchronize(H->stream);
+    for (int k = 0; k < 2 * HTLR_NUM_STAGES; ++k) cudaEventDestroy(tev.ev[k]);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    for (int k = 0; k < HTLR_NUM_STAGES; ++k) stage_ms[k] = tev.ms[k];
+    return HTLR_OK;
+}
+
+int htlr_matvec_host(htlr_handle *H, const double *u_host, double *f_host, int nrhs)
+{
+    if (!is_live(H)) return fail(HTLR_EINVAL, "not a live HTLR handle");
+    if (!u_host || !f_host) return fail(HTLR_EINVAL, "u and f must not be NULL");
+    if (nrhs < 1) return fail(HTLR_EINVAL, "nrhs must be >= 1");
+    const size_t N = (size_t)ipow(H->n, H->d);
+    size_t need = N * (size_t)nrhs;
+    if (need > H->stage_cap) {
+        if (H->d_stage_u) cudaFree(H->d_stage_u);
+        if (H->d_stage_f) cudaFree(H->d_stage_f);
+        H->d_stage_u = H->d_stage_f = nullptr;
+        H->stage_cap = 0;
+        HTLR_CK(cudaMalloc(&H->d_stage_u, need * sizeof(double)));
+        HTLR_CK(cudaMalloc(&H->d_stage_f, need * sizeof(double)));
+        H->stage_cap = need;
+    }
+    HTLR_CK(cudaMemcpyAsync(H->d_stage_u, u_host, need * sizeof(double), cudaMemcpyHostToDevice,
+                            H->stream));
+    int rc = enqueue_matvec(H, H->d_stage_u, H->d_stage_f, nrhs);
+    if (rc) return rc;
+    HTLR_CK(cudaMemcpyAsync(f_host, H->d_stage_f, need * sizeof(double), cudaMemcpyDeviceToHost,
+                            H->stream));
+    HTLR_CK(cudaStreamSynchronize(H->stream));
+    return HTLR_OK;
+}
+
+void htlr_free(htlr_handle *H)
+{
+    if (!H) return;
+    {
+        std::lock_guard<std::mutex> g(g_live_mu);
+        if (!g_live.count(H)) {
+            set_error("htlr_free: not a live HTLR handle (double free?)");
+            return;
+        }
+        g_live.erase(H);
+    }
+    cudaStreamSynchronize(H->stream);
+    destroy(H);
+}
+
+int htlr_info(const htlr_handle *H, htlr_stats *s)
+{
+    if (!is_live(H)) return fail(HTLR_EINVAL, "not a live HTLR handle");
+    if (!s) return fail(HTLR_EINVAL, "stats pointer must not be NULL");
+    *s = H->stats;
+    return HTLR_OK;
+}
+
+int htlr_set_stream(htlr_handle *H, void *stream)
+{
+    if (!is_live(H)) return fail(HTLR_EINVAL, "not a live HTLR handle");
+    H->stream = (cudaStream_t)stream;
+    return HTLR_OK;
+}
+
+int htlr_sync(const htlr_handle *H)
+{
+    if (!is_live(H)) return fail(HTLR_EINVAL, "not a live HTLR handle");
+    HTLR_CK(cudaStreamSynchronize(H->stream));
+    int err = 0;
+    HTLR_CK(cudaMemcpy(&err, H->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) {
+        char buf[96];
+        snprintf(buf, sizeof buf, "device check failed (code %d)", err);
+        return fail(HTLR_EDEVICE, buf);
+    }
+    return HTLR_OK;
+}
+
+int htlr_last_launch_count(const htlr_handle *H)
+{
+    if (!is_live(H)) return -1;
+    return H->last_launches;
+}
+
+}  // extern "C"

@@ -1,0 +1,174 @@
+// Internal declarations of the HTLR CUDA library (not part of the C ABI).
+//
+// Device data layout (uniform grid, natural point order i_1 + n i_2 + n^2 i_3):
+//   * boxes of level l are numbered lexicographically, b_1 + 2^l b_2 + 4^l b_3;
+//   * per level: one interpolation factor F_l (nb x pe, column-major) shared by every box
+//     and dimension (the points sit at the same place in every box of a uniform grid),
+//     orthonormal after the QR of Algorithm 1, and the triangular R_l (pe x p);
+//   * admissible blocks of level l: CSR by target box tau (column = source box sigma,
+//     core = index of the core tensor); a core is stored column-major [s][t] with
+//     leading dimension ld = pd rounded up to 32 doubles (pd = pe^d), so every column
+//     starts 256-byte aligned;
+//   * inadmissible leaves: CSR by leaf tau, dense blocks [j][i] (leaf-local lexicographic
+//     indices), same padding rule;
+//   * matvec work arrays: W_l, H_l of shape [box][rhs][pd] for an RHS chunk.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/htlr.h"
+
+namespace htlr {
+
+constexpr uint64_t kMagicLive = 0x48544c52474233ull;
+constexpr uint64_t kMagicDead = 0x64656164deadull;
+constexpr int kMaxD = 3;
+constexpr int kMaxP = 16;
+
+// Device error codes written into the handle's error word.
+enum DevErr : int { kDevOk = 0, kDevBadIndex = 1, kDevBadTask = 2 };
+
+struct KernelDesc {
+    int type;
+    double scale;
+    double param;
+};
+
+// One unit of streaming work: entries [e0, e1) of row `row` of list `kind`.
+// kind 0..L: admissible blocks of that level; kind L+1: inadmissible leaves.
+struct Task {
+    int kind;
+    int row;
+    int e0, e1;
+    long long part;  // offset of this task's partial result (doubles)
+};
+
+// Per-kind description used by the streaming kernel (kept in device memory).
+struct KindDesc {
+    const int *col;      // source box per entry
+    const int *blk;      // block (core / dense) index per entry
+    const double *blocks;
+    long long blk_stride;  // doubles between consecutive blocks (ld * cols)
+    int ld;              // padded rows of a block
+    int rows;            // real rows (pd_out)
+    int cols;            // pd_in
+    int rpl;             // rows per lane = ld / 32
+    int is_near;         // 1: x gathered from u (natural order)
+    const double *x;     // far: W of the level ([box][rhs][pd])
+    long long x_box_stride;  // doubles per box in x (nrc * pd)
+};
+
+struct LevelData {
+    int level = 0, nb = 0, nbox1 = 0, nbox = 0, pe = 0, pd = 0, ld = 0;
+    int64_t nfar = 0;
+    std::vector<int> far_rowptr, far_col, far_core;
+    int *d_far_rowptr = nullptr, *d_far_col = nullptr, *d_far_core = nullptr;
+    double *d_F = nullptr;      // nb x pe
+    double *d_R = nullptr;      // pe x p
+    double *d_cores = nullptr;  // ncores x (ld * pd)
+    int64_t ncores = 0;
+    double *d_W = nullptr, *d_H = nullptr;  // nbox x nrc x pd
+    int task0 = 0, task1 = 0;               // task range (far) of this level
+    std::vector<int> row_task_begin;        // per tau: first task; size nbox + 1
+    int *d_row_task = nullptr;
+};
+
+struct Plan;  // forward
+
+}  // namespace htlr
+
+struct htlr_handle {
+    uint64_t magic = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    htlr::KernelDesc kern{};
+    int d = 0, n = 0, leaf = 0, p = 0, L = 0, orth = 1, q = 16;
+    double eta = 0.0;
+    int storage = HTLR_STORE_STORED;
+    int nrc = 1;  // RHS per chunk
+    double h = 0.0, wgt = 0.0;  // grid step and quadrature weight h^d
+    double diag = 0.0;          // K_ii h^d (uniform grid)
+    double *d_a = nullptr;      // a(x) natural order or null
+    std::vector<htlr::LevelData> lev;  // levels 0..L
+    // inadmissible leaves
+    int64_t nnear = 0, nnear_unique = 0;
+    std::vector<int> near_rowptr, near_col, near_blk;
+    int *d_near_rowptr = nullptr, *d_near_col = nullptr, *d_near_blk = nullptr;
+    double *d_near = nullptr;
+    int near_ld = 0, near_rows = 0;
+    std::vector<int> near_row_task;  // per leaf: first task, size nleaf + 1
+    int *d_near_row_task = nullptr;
+    // streaming tasks
+    std::vector<htlr::Task> tasks;
+    htlr::Task *d_tasks = nullptr;
+    htlr::KindDesc *d_kinds = nullptr;
+    std::vector<htlr::KindDesc> kinds;
+    double *d_part = nullptr;
+    long long part_doubles = 0;
+    int max_cols = 1;
+    int *d_err = nullptr;
+    // host staging for htlr_matvec_host
+    double *d_stage_u = nullptr, *d_stage_f = nullptr;
+    size_t stage_cap = 0;
+    int last_launches = 0;
+    htlr_stats stats{};
+    std::vector<void *> allocs;
+};
+
+namespace htlr {
+
+// Error reporting (thread-local message).
+void set_error(const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+
+// ---- plan.cu: block cluster tree walk -------------------------------------------
+// Counts (pass 0) or fills (pass 1) the far and near lists of level `level` from the
+// near list of level-1.  Boxes are lexicographic.  Strong admissibility when eta > 0.
+void launch_walk(int pass, int d, int level, double eta, const int *d_prev_rowptr,
+                 const int *d_prev_col, int *d_far_cnt, int *d_near_cnt,
+                 const int *d_far_off, const int *d_near_off, int *d_far_col, int *d_near_col,
+                 cudaStream_t s);
+
+// ---- construct.cu -----------------------------------------------------------------
+// Interpolation factor of a level (barycentric Lagrange on Chebyshev points) and, if
+// orth, its economy QR; writes F (nb x pe) and R (pe x p; identity-padded if !orth).
+void launch_factor(int nb, int p, int pe, double side, double h, int orth, double *d_F,
+                   double *d_R, cudaStream_t s);
+// Diagonal K_ii w_i on the uniform grid: int over the cell of k(center, y) dy.
+void launch_diag(const KernelDesc &k, int d, double h, int q, const double *d_gx,
+                 const double *d_gw, double *d_out, cudaStream_t s);
+// Core tensors: for each core c, offset (tau - sigma) in boxes from d_off[c*3..]; writes
+// wgt * k(xi_t, eta_s) transformed by R on all 2d modes, [s][t] with leading dim ld.
+void launch_cores(const KernelDesc &k, int d, int p, int pe, int ld, int apply_r, double side,
+                  double wgt, const double *d_R, int64_t ncores, const int *d_off,
+                  double *d_cores, double *d_scratch, int nscratch_ctas, cudaStream_t s);
+// Dense blocks of inadmissible leaves: block b between leaves with offset d_off[b*3..]
+// (tau - sigma) and, for STORED, target leaf d_tau[b] (to add a on the diagonal).
+void launch_near(const KernelDesc &k, int d, int n, int leaf, int ld, double h, double wgt,
+                 double diag, const double *d_a, int64_t nblk, const int *d_off,
+                 const int *d_tau, double *d_blocks, cudaStream_t s);
+
+// ---- apply.cu -------------------------------------------------------------------
+void launch_up(int d, int n, int level, int nb, int pe, const double *d_F, const double *u,
+               int nrhs_here, long long ldu, int nrc, double *d_W, cudaStream_t s);
+// streaming = true marks the blocks as read once per matvec (evict-first loads).
+void launch_stream(const Task *d_tasks, int ntasks, const KindDesc *d_kinds, int max_rpl,
+                   int d, int n, int leaf, const double *u, long long ldu, int nrhs_here,
+                   int max_cols, double *d_part, int *d_err, bool streaming, cudaStream_t s);
+void launch_reduce_far(int nbox, int pd, int ld, int nrc, int nrhs_here, const int *d_row_task,
+                       const Task *d_tasks, const double *d_part, double *d_H, cudaStream_t s);
+struct DownLevel {
+    int level, nb, pe, pd;
+    const double *F;
+    const double *H;
+};
+void launch_out(int d, int n, int leaf, int L, int nrc, int nrhs_here, const int *d_near_row_task,
+                const Task *d_tasks, const double *d_part, int near_ld, const double *d_a_add,
+                const double *u, long long ldu, const DownLevel *d_down, int ndown, double *f,
+                long long ldf, cudaStream_t s);
+
+}  // namespace htlr

@@ -1,0 +1,156 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Bar: FP64 mode matches the oracle's HTLR (Algorithms 1-2) to a per-RHS relative 2-norm
+of 1e-12 (the tolerance stated for FP64 mode), and the dense Nystrom product to the
+interpolation accuracy; integer structure (block counts) is compared exactly.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from _helpers import gpu_matvec, rel
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2508_05958_gb300 import htlr
+    htlr.load()
+
+
+def _oracle_htlr(oracle, w, u, **kw):
+    args = dict(a=w.a(), scale=w.kscale, param=w.kparam)
+    args.update(kw)
+    H = oracle.HTLR(w.d, w.n, args.pop("ktype", w.ktype), args.pop("leaf", w.leaf),
+                    args.pop("p", w.p), args.pop("eta", w.eta), **args)
+    return H.matvec(u), H.stats()
+
+
+def test_c1_full_against_oracle_and_dense(oracle):
+    from paper_2508_05958_gb300.workloads import workload
+    w = workload("c1")
+    u = w.u()
+    f, info = gpu_matvec(w, u)
+    ref, st = _oracle_htlr(oracle, w, u)
+    assert info["far_per_level"] == st[0] and info["near_blocks"] == st[1]
+    assert rel(f, ref) < TOL
+    fd = oracle.dense_rows(w.d, w.n, w.ktype, u, a=w.a())
+    assert rel(f, fd) < 1e-6
+
+
+def test_c2_full_against_oracle_and_dense(oracle):
+    from paper_2508_05958_gb300.workloads import workload
+    w = workload("c2")
+    u = w.u()
+    f, info = gpu_matvec(w, u, storage=1)
+    assert info["storage"] == 1 and info["p_eff_leaf"] == 4
+    ref, st = _oracle_htlr(oracle, w, u)
+    assert info["far_per_level"] == st[0] == [0, 0, 1416, 133944]
+    assert info["near_blocks"] == st[1] == 37576
+    assert abs(info["paper_storage_doubles"] - st[2]) < 0.5
+    assert rel(f, ref) < TOL
+    rows = w.sample_rows(512)
+    fd = oracle.dense_rows(w.d, w.n, w.ktype, u, rows=rows, a=w.a())
+    assert rel(f[rows], fd) < 1e-6
+
+
+@pytest.mark.parametrize("storage", [1, 2])
+@pytest.mark.parametrize("case", [
+    dict(d=2, n=32, leaf=4, p=4, eta=math.sqrt(2)),
+    dict(d=2, n=64, leaf=8, p=3, eta=0.0),
+    dict(d=3, n=16, leaf=4, p=3, eta=1.0),
+    dict(d=3, n=16, leaf=2, p=3, eta=0.0),      # wide leaf factors: p_eff = 2 < p
+    dict(d=3, n=8, leaf=4, p=2, eta=1.0),       # one level below the root
+])
+def test_polynomial_kernel_exact(oracle, case, storage):
+    """Per-dimension degree p-1 is reproduced exactly: GPU == dense product."""
+    from paper_2508_05958_gb300.workloads import Workload
+    w = Workload("poly", d=case["d"], n=case["n"], ktype=4, leaf=case["leaf"], p=case["p"],
+                 eta=case["eta"], kparam=case["p"] - 1, a_kind="one", seed=21)
+    u = w.u(nrhs=3)
+    f, info = gpu_matvec(w, u, storage=storage)
+    assert info["storage"] == storage
+    fd = oracle.dense_rows(w.d, w.n, 4, u, param=w.kparam, a=w.a())
+    assert rel(f, fd) < 1e-13
+    ref, _ = _oracle_htlr(oracle, w, u)
+    assert rel(f, ref) < TOL
+
+
+@pytest.mark.parametrize("orth", [0, 1])
+@pytest.mark.parametrize("storage", [1, 2])
+def test_orth_and_storage_modes_match_oracle(oracle, orth, storage):
+    from paper_2508_05958_gb300.workloads import workload
+    w = workload("c2", n=16, leaf=2, p=4)
+    u = w.u(nrhs=2)
+    f, _ = gpu_matvec(w, u, storage=storage, orth=orth)
+    ref, _ = _oracle_htlr(oracle, w, u, orth=bool(orth))
+    assert rel(f, ref) < TOL
+
+
+@pytest.mark.parametrize("nrhs", [1, 2, 4, 5, 9])
+def test_multi_rhs_chunks_and_ragged_tail(oracle, nrhs):
+    from paper_2508_05958_gb300.workloads import workload
+    w = workload("c1", n=32)
+    u = w.u(nrhs=nrhs)
+    f, _ = gpu_matvec(w, u)
+    ref, _ = _oracle_htlr(oracle, w, u)
+    assert f.shape == (w.N, nrhs)
+    assert rel(f, ref) < TOL
+
+
+@pytest.mark.parametrize("ktype,kscale,kparam", [(0, -1 / (2 * math.pi), 0.0), (2, 1.0, 0.0),
+                                                 (3, 1.0, math.sqrt(2)), (5, 0.7, 0.0)])
+def test_other_kernels_2d(oracle, ktype, kscale, kparam):
+    from paper_2508_05958_gb300.workloads import Workload
+    w = Workload("k", d=2, n=64, ktype=ktype, leaf=8, p=5, eta=math.sqrt(2), kscale=kscale,
+                 kparam=kparam, a_kind="one", seed=5)
+    u = w.u(nrhs=1)
+    f, _ = gpu_matvec(w, u)
+    ref, _ = _oracle_htlr(oracle, w, u)
+    assert rel(f, ref) < TOL
+
+
+def test_weak_admissibility_3d_gaussian(oracle):
+    from paper_2508_05958_gb300.workloads import Workload
+    w = Workload("g", d=3, n=32, ktype=3, leaf=4, p=4, eta=0.0, kparam=math.sqrt(3), seed=6)
+    u = w.u(nrhs=1)
+    f, info = gpu_matvec(w, u)
+    ref, st = _oracle_htlr(oracle, w, u)
+    assert info["far_per_level"] == st[0]
+    assert rel(f, ref) < TOL
+
+
+def test_host_entry_point_and_determinism(oracle):
+    from paper_2508_05958_gb300.workloads import workload
+    w = workload("c2", n=16, leaf=4)
+    u = w.u(nrhs=3)
+    outs, _ = gpu_matvec(w, u, repeat=3)
+    assert all(np.array_equal(outs[0], o) for o in outs[1:])     # bitwise repeatable
+    fh, _ = gpu_matvec(w, u, host=True)
+    assert np.array_equal(fh, outs[0])
+
+
+def test_diagonal_value_matches_closed_form():
+    from paper_2508_05958_gb300 import htlr
+    h = 1.0 / 32
+    H = htlr.htlr_construct(1, 3, 32, 4, 5, 1.0)
+    try:
+        dv = htlr.htlr_info(H)["diag_value"]
+    finally:
+        htlr.htlr_free(H)
+    exact = (3 * math.log(2 + math.sqrt(3)) - math.pi / 2) * h * h
+    assert abs(dv - exact) < 2e-5 * exact
+
+
+def test_memory_limit_refusal():
+    from paper_2508_05958_gb300 import htlr
+    with pytest.raises(htlr.HTLRError) as ei:
+        htlr.htlr_construct(1, 3, 32, 4, 5, 1.0, storage=1, hbm_limit=1 << 20)
+    assert ei.value.code == htlr.HTLR_ENOMEM
