@@ -119,6 +119,10 @@ CONFIGS = {
                    a_kind="sin", u_kind="normal", seed=2),
     "c3": Workload("c3", d=3, n=128, ktype=K_INV_R, leaf=8, p=6, eta=1.0, nrhs=64,
                    a_kind="zero", u_kind="normal", seed=3),
+    # the c2 grid under weak admissibility: the same block shapes (125 x 125 cores at
+    # level 2, 64 x 64 at the leaves) but ~0.2 GB of blocks: the profiling case
+    "c2_weak": Workload("c2_weak", d=3, n=32, ktype=K_INV_R, leaf=4, p=5, eta=0.0, nrhs=1,
+                        a_kind="sin", u_kind="normal", seed=2),
     "c4": Workload("c4", d=3, n=128, ktype=K_EXP_R, leaf=8, p=7, eta=1.0, nrhs=16,
                    a_kind="zero", u_kind="normal", grid_kind="quasi", seed=4),
 }
