@@ -94,6 +94,11 @@ def lib():
                                         ctypes.c_double, _D, _D, ctypes.c_int, _I32, _I32,
                                         ctypes.c_int, ctypes.c_double, ctypes.c_int, _I32, _I32,
                                         _D, _D, _D]
+            L.orc_htlr_matvec_range.restype = ctypes.c_double
+            L.orc_htlr_matvec_range.argtypes = [ctypes.c_void_p, _D, _D, ctypes.c_long,
+                                                ctypes.c_long]
+            L.orc_htlr_nblocks.restype = ctypes.c_long
+            L.orc_htlr_nblocks.argtypes = [ctypes.c_void_p]
             L.orc_num_threads.restype = ctypes.c_int
             L.orc_num_threads.argtypes = []
             _lib = L
@@ -233,6 +238,16 @@ class HTLR:
         F = np.zeros_like(U, order="F")
         lib().orc_htlr_matvec(self._h, U.ctypes.data_as(_D), U.shape[1], F.ctypes.data_as(_D))
         return F[:, 0] if vec else F
+
+    def nblocks(self):
+        return lib().orc_htlr_nblocks(self._h)
+
+    def matvec_range(self, u, f, k0, k1):
+        """Accumulate blocks k0..k1-1 (recursion order) of A u into f (one RHS, both
+        float64 arrays of length N); returns the multiply-adds of those blocks."""
+        assert u.dtype == np.float64 and f.dtype == np.float64 and u.size == f.size == self.N
+        return lib().orc_htlr_matvec_range(self._h, u.ctypes.data_as(_D), f.ctypes.data_as(_D),
+                                           k0, k1)
 
     def stats(self):
         far = np.zeros(40, dtype=np.int64)

@@ -1146,3 +1146,28 @@ int orc_dense_rows_api(int d, int n, int ktype, double kscale, double kparam,
     free(H.xbuf); free(H.ebuf); free(H.abuf);
     return rc;
 }
+
+/* Algorithm 2 restricted to the blocks k0..k1-1 (recursion order), accumulated into f
+ * for one right-hand side (f is not cleared).  Returns the multiply-adds of the core and
+ * dense products of those blocks, so that a timed slice can be scaled to the whole
+ * product; a bounded sample of the full HMultVec. */
+double orc_htlr_matvec_range(const orc_htlr *H, const double *u, double *f, long k0, long k1)
+{
+    double work = 0.0;
+    int d = H->P.d;
+    if (k0 < 0) k0 = 0;
+    if (k1 > H->nblk) k1 = H->nblk;
+    for (long k = k0; k < k1; ++k) {
+        const orc_block *K = &H->blk[k];
+        apply_block(&H->P, K, u, f);
+        double a = 1.0, b = 1.0;
+        for (int l = 0; l < d; ++l) {
+            if (K->far) { a *= K->pt[l]; b *= K->ps[l]; }
+            else { a *= K->tau.cnt[l]; b *= K->sig.cnt[l]; }
+        }
+        work += a * b;
+    }
+    return work;
+}
+
+long orc_htlr_nblocks(const orc_htlr *H) { return H->nblk; }
