@@ -163,6 +163,29 @@ int htlr_matvec_host(htlr_handle *H, const double *u_host, double *f_host, int n
 int htlr_matvec_timed(const htlr_handle *H, const double *u, double *f, int nrhs,
                       float *stage_ms);
 
+/*
+ * htlr_matvec_noalloc -- f = A u, like htlr_matvec, but without any device allocation:
+ * its scratch (the per-level contracted tensors W and H, the partial sums of the block
+ * stream and a small task table) is taken from one fixed array of 64 MiB that the library
+ * declares statically, instead of the handle's own work buffers.  The paper has no
+ * counterpart; this exists for callers that cannot call cudaMalloc when they apply an
+ * operator: processes whose device memory is fully reserved by a pool or a budget,
+ * latency-bound loops that must not block in cudaMalloc / cudaFree (cudaFree waits for
+ * the whole device), or a caller applying a handle it shares with other threads.
+ *   u, f   device pointers as for htlr_matvec (caller-owned, must not overlap).
+ * Limits and behaviour:
+ *   - operators whose scratch would exceed 64 MiB are rejected with HTLR_ENOMEM and a
+ *     message giving the size needed (e.g. c2, d=3 n=32, needs about 51 MB; the
+ *     n=128 operators do not fit: use htlr_matvec);
+ *   - the first call on a device looks up the array's device address there (with that
+ *     device current); make that first call before any CUDA stream capture;
+ *   - every call on a device shares the same array: calls whose GPU work overlaps (other
+ *     streams, other threads) race; nothing needs clearing between calls;
+ *   - every GPU that loads the library holds the 64 MiB until the process exits.
+ * Asynchronous on the handle's stream; the current device must be the handle's device.
+ */
+int htlr_matvec_noalloc(const htlr_handle *H, const double *u, double *f, int nrhs);
+
 /* Release everything the handle owns.  NULL is a no-op.  A second free of the same
  * handle is detected through a magic word and ignored (reported by htlr_last_error). */
 void htlr_free(htlr_handle *H);

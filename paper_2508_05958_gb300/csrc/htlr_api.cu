@@ -585,6 +585,8 @@ struct StageEvents {
     float ms[HTLR_NUM_STAGES];
 };
 
+bool handle_is_live(const htlr_handle *H) { return is_live(H); }
+
 static int enqueue_matvec(const htlr_handle *H, const double *u, double *f, int nrhs,
                           StageEvents *tev = nullptr)
 {

@@ -22,7 +22,7 @@ MAX_LEVELS = 16
 
 NUM_STAGES = 4
 SYMBOLS = ("htlr_construct", "htlr_construct_ex", "htlr_matvec", "htlr_matvec_timed",
-           "htlr_matvec_host", "htlr_free",
+           "htlr_matvec_host", "htlr_matvec_noalloc", "htlr_free",
            "htlr_info", "htlr_set_stream", "htlr_sync", "htlr_last_error",
            "htlr_last_launch_count")
 
@@ -94,6 +94,8 @@ def load(build_if_missing: bool = True):
         L.htlr_matvec.restype = ctypes.c_int
         L.htlr_matvec_timed.argtypes = [vp, vp, vp, ctypes.c_int, P(ctypes.c_float)]
         L.htlr_matvec_timed.restype = ctypes.c_int
+        L.htlr_matvec_noalloc.argtypes = [vp, vp, vp, ctypes.c_int]
+        L.htlr_matvec_noalloc.restype = ctypes.c_int
         L.htlr_matvec_host.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_double), ctypes.c_int]
         L.htlr_matvec_host.restype = ctypes.c_int
         L.htlr_free.argtypes = [vp]
@@ -175,6 +177,14 @@ def htlr_matvec(H, u, f, nrhs=None):
     if nrhs is None:
         nrhs = 1 if u.dim() == 1 else u.shape[0]
     _check(load().htlr_matvec(H, _dptr(u), _dptr(f), nrhs))
+
+
+def htlr_matvec_noalloc(H, u, f, nrhs=None):
+    """f = A u like htlr_matvec, with the library's static 64 MiB scratch instead of any
+    device allocation (for callers that cannot allocate; calls on a device share it)."""
+    if nrhs is None:
+        nrhs = 1 if u.dim() == 1 else u.shape[0]
+    _check(load().htlr_matvec_noalloc(H, _dptr(u), _dptr(f), nrhs))
 
 
 def htlr_matvec_timed(H, u, f, nrhs=None):
