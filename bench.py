@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--impl", default="htlr", choices=["htlr", "reference"])
     ap.add_argument("--config", default="c2")
     ap.add_argument("--storage", type=int, default=1, help="1 STORED, 2 SHARED, 0 AUTO")
+    ap.add_argument("--far-precision", type=int, default=1, help="0 FP64, 1 DF64, 2 FP32")
+    ap.add_argument("--near-precision", type=int, default=1, help="0 FP64, 1 DF64, 2 FP32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-s", type=float, default=20.0)
     return ap.parse_args()
@@ -52,10 +54,15 @@ def dist_env():
     return rank, world, local
 
 
+def dtype_name(info):
+    fp, np_ = PREC_NAME[info["far_precision"]], PREC_NAME[info["near_precision"]]
+    return fp if fp == np_ else f"{fp} far / {np_} near"
+
+
 def workload_desc(w, storage_name):
     kern = {0: "log|x-y|", 1: "1/|x-y|", 2: "exp(-|x-y|)", 3: "gauss", 4: "poly", 5: "const"}[w.ktype]
     return (f"{w.name}: d={w.d} n={w.n} N={w.N} kernel {kern} a={w.a_kind} leaf {w.leaf}^{w.d} "
-            f"p={w.p} eta={w.eta:.4g} nrhs={w.nrhs} FP64 {storage_name}")
+            f"p={w.p} eta={w.eta:.4g} nrhs={w.nrhs} {storage_name}")
 
 
 # ----------------------------------------------------------------------------------
@@ -196,20 +203,62 @@ def run_reference(args, w):
 # ----------------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------------
-def algorithmic_stream_bytes(info, w):
-    """Bytes the stream kernel must read per launch: every admissible block's core
-    (p_eff^d x p_eff^d doubles) and every inadmissible block (|tau| x |sigma| doubles)."""
-    d = w.d
-    total = 0.0
+PREC_NAME = {0: "f64", 1: "df64", 2: "f32"}
+PREC_BYTES = {0: 8, 1: 8, 2: 4}
+# multiply-adds per second of the stream's inner loop, from unit counts and clocks
+# (152 SMs at 2.07 GHz): FP64 2 FMA/clk/SM (the nominal 1.25 TFLOP/s); FP32 128 lanes;
+# df64 spends 12 FP32-pipe instructions per multiply-add (see stream_impl.cuh)
+ALU_PEAK = {0: 152 * 2 * 2.07e9, 1: 152 * 128 * 2.07e9 / 12, 2: 152 * 128 * 2.07e9}
+
+
+def stream_elements(info, w):
+    """Elements (multiply-adds per RHS) of the block stream: every admissible block's core
+    (p_eff^d x p_eff^d) and every inadmissible block (|tau| x |sigma|), split into far and
+    near, plus the elements actually held (unique blocks, for SHARED storage)."""
+    far = far_unique = 0.0
     for lv, nfar in enumerate(info["far_per_level"]):
         if nfar == 0:
             continue
-        nb = w.n >> lv
-        pe = min(w.p, nb)
-        total += nfar * (pe ** d) ** 2 * 8.0
-    rows = w.leaf ** d
-    total += info["near_blocks"] * rows * rows * 8.0
-    return total
+        pe = min(w.p, w.n >> lv)
+        far += nfar * float(pe ** w.d) ** 2
+    rows = float(w.leaf ** w.d)
+    near = info["near_blocks"] * rows * rows
+    if info["storage"] == 1:
+        far_unique, near_unique = far, near
+    else:
+        # SHARED: held blocks are the unique ones (bytes_cores / bytes_near already count
+        # the padded storage; use them directly)
+        far_unique = info["bytes_cores"] / PREC_BYTES[info["far_precision"]]
+        near_unique = info["bytes_near"] / PREC_BYTES[info["near_precision"]]
+    return far, near, far_unique, near_unique
+
+
+def stream_roofline(info, w, nrhs, stream_ms, hbm_peak, hbm_src):
+    fp, np_ = info["far_precision"], info["near_precision"]
+    far, near, far_u, near_u = stream_elements(info, w)
+    t = stream_ms * 1e-3
+    hbm_bytes = far_u * PREC_BYTES[fp] + near_u * PREC_BYTES[np_]
+    t_hbm = hbm_bytes / (hbm_peak * 1e9)
+    t_alu = (far / ALU_PEAK[fp] + near / ALU_PEAK[np_]) * nrhs
+    macs = (far + near) * nrhs
+    base = {"kernel": "stream_kernel", "kernel_ms": stream_ms,
+            "algorithmic_bytes_per_launch": hbm_bytes, "multiply_adds_per_launch": macs,
+            "hbm_achieved_gbs": hbm_bytes / t / 1e9,
+            "hbm_frac_of_measured": hbm_bytes / t / 1e9 / hbm_peak, "traffic": None,
+            "precision": {"far": PREC_NAME[fp], "near": PREC_NAME[np_]}}
+    if t_alu > t_hbm:
+        peak = 2 * macs / t_alu / 1e12
+        ach = 2 * macs / t / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak,
+                "peak_source": "derived: 152 SMs x 2.07 GHz x (FP64 2 FMA/clk | FP32 128 "
+                               "FMA/clk | df64 128/12 multiply-adds/clk), FP64-equivalent flops"}
+    else:
+        ach = hbm_bytes / t / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                "frac": ach / hbm_peak, "peak_source": hbm_src}
+    roof.update(base)
+    return roof
 
 
 def run_gpu(args, w):
@@ -230,15 +279,15 @@ def run_gpu(args, w):
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    fp64_peak_tflops = 1.25   # nominal GB300 FP64 rate (recipe table)
 
     t0 = time.perf_counter()
     H = htlr.htlr_construct(w.ktype, w.d, w.n, w.leaf, w.p, w.eta, kscale=w.kscale,
-                            kparam=w.kparam, a=w.a(), storage=args.storage, stream=stream)
+                            kparam=w.kparam, a=w.a(), storage=args.storage, stream=stream,
+                            far_precision=args.far_precision, near_precision=args.near_precision)
     torch.cuda.synchronize()
     construct_s = time.perf_counter() - t0
     info = htlr.htlr_info(H)
-    storage_name = {1: "STORED", 2: "SHARED"}.get(info["storage"], "?")
+    storage_name = {1: "STORED", 2: "SHARED"}.get(info["storage"], "?") + " " + dtype_name(info)
     nrhs = w.nrhs
     U = w.u(nrhs=nrhs)
     with torch.cuda.stream(stream):
@@ -285,23 +334,7 @@ def run_gpu(args, w):
     stage_ms = stage / args.steps
 
     # roofline of the dominant kernel (the block stream)
-    alg_bytes = algorithmic_stream_bytes(info, w)
-    stream_ms = stage_ms[1]
-    achieved_gbs = alg_bytes / (stream_ms * 1e-3) / 1e9
-    fp64_tflops = alg_bytes / 8.0 * 2.0 * nrhs / (stream_ms * 1e-3) / 1e12
-    # which roof binds: FP64 pipe (1 FMA per streamed double) or HBM
-    t_hbm = alg_bytes / (hbm_peak * 1e9)
-    t_fp = alg_bytes / 8.0 * 2.0 * nrhs / (fp64_peak_tflops * 1e12)
-    if t_fp > t_hbm:
-        roof = {"bound": "alu", "achieved": fp64_tflops, "peak": fp64_peak_tflops,
-                "unit": "TFLOP/s", "frac": fp64_tflops / fp64_peak_tflops,
-                "peak_source": "nominal GB300 FP64 rate 1.25 TFLOP/s (152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz)"}
-    else:
-        roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved_gbs / hbm_peak, "peak_source": hbm_src}
-    roof.update({"kernel": "stream_kernel", "algorithmic_bytes_per_launch": alg_bytes,
-                 "kernel_ms": stream_ms, "hbm_achieved_gbs": achieved_gbs,
-                 "hbm_frac_of_measured": achieved_gbs / hbm_peak, "traffic": None})
+    roof = stream_roofline(info, w, nrhs, stage_ms[1], hbm_peak, hbm_src)
 
     # end to end through the host-buffer entry point (pinned host memory, copies timed)
     uh = torch.from_numpy(np.ascontiguousarray(U.T)).pin_memory().numpy()
@@ -319,9 +352,9 @@ def run_gpu(args, w):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": dtype_name(info), "data": "synthetic",
         "config": {"workload": workload_desc(w, storage_name), "l2": "flushed between steps "
-                   "(256 MB write); blocks streamed per step: %.2f GB" % (alg_bytes / 1e9),
+                   "(256 MB write); block bytes held: %.3f GB" % (roof["algorithmic_bytes_per_launch"] / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "construct_s": construct_s, "stage_ms": {"up": stage_ms[0],
                    "stream": stage_ms[1], "reduce": stage_ms[2], "out": stage_ms[3]},

@@ -84,6 +84,16 @@ typedef enum {
                                dense block) per (level, offset) is kept */
 } htlr_storage;
 
+/* Arithmetic of the far-field (core) and near-field (dense block) products. */
+typedef enum {
+    HTLR_PREC_FP64 = 0,  /* FP64 blocks and FP64 fused multiply-adds */
+    HTLR_PREC_DF64 = 1,  /* FP64 blocks held as float pairs (hi + lo, 48-bit significand) and
+                            products formed with error-free FP32 transformations; results
+                            within ~1e-14 of FP64.  Entries must lie within FP32 range,
+                            |x| in [1e-30, 1e30], for that accuracy */
+    HTLR_PREC_FP32 = 2   /* FP32 blocks, products and accumulation (~1e-7 relative) */
+} htlr_precision;
+
 typedef struct {
     int storage;       /* htlr_storage (default AUTO) */
     int orth;          /* 1: QR-orthonormalise the factors (Algorithm 1), 0: keep the
@@ -92,6 +102,8 @@ typedef struct {
                           integral (default 16, range 1..64) */
     void *stream;      /* cudaStream_t for construction and matvecs (NULL: default stream) */
     size_t hbm_limit;  /* maximum bytes the handle may allocate (0: 90% of free memory) */
+    int far_precision;   /* htlr_precision of the admissible blocks (default FP64) */
+    int near_precision;  /* htlr_precision of the inadmissible blocks (default FP64) */
 } htlr_options;
 
 /* Statistics of a constructed operator (htlr_info). */
@@ -109,6 +121,7 @@ typedef struct {
                                          near block |tau| |sigma| (Prop. 3.4/3.5, §5) */
     size_t bytes_cores, bytes_near, bytes_factors, bytes_work, bytes_total;
     double diag_value;                /* K_ii w_i on the uniform grid (eq. (1.4)) */
+    int far_precision, near_precision;  /* htlr_precision in use */
 } htlr_stats;
 
 typedef struct htlr_handle htlr_handle;

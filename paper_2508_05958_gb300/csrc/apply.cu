@@ -91,165 +91,22 @@ void launch_up(int d, int n, int level, int nb, int pe, const double *d_F, const
     up_kernel<<<grid, 128, smem, s>>>(d, n, level, nb, pe, d_F, u, ldu, nrc, d_W, slab);
 }
 
-// ---------------------------------------------------------------------------------
-// stream: one warp per task.  A task is a run of consecutive entries of one row of a
-// block list; for every entry the warp stages x_sigma (W_sigma, or u_sigma gathered
-// from natural order for inadmissible leaves) in shared memory, then streams the block
-// column by column: lane l owns rows l, l + 32, ... (RPL of them), so every load of a
-// column is one coalesced 256-byte access.  The task's partial result goes to `part`;
-// the reduction over a row's tasks is done in a fixed order afterwards (deterministic).
-// ---------------------------------------------------------------------------------
-// Block loads: evict-first when every block is read once per matvec (STORED), plain
-// cached loads when blocks are shared by many boxes (SHARED) and should stay in L2.
-template <bool CS>
-__device__ __forceinline__ double ldblk(const double *p)
+// The block stream (the hot loop) lives in stream_impl.cuh, instantiated per
+// precision in stream_fp64.cu, stream_df64.cu and stream_fp32.cu.
+void launch_stream(int prec, const StreamArgs &a)
 {
-    if (CS) return __ldcs(p);
-    return __ldg(p);
-}
-
-template <int RPL, int NR, bool CS>
-__device__ __forceinline__ void stream_task(const Task &T, const KindDesc &K, int lane,
-                                            double *xs, int d, int n, int leaf, int nl_level,
-                                            const double *__restrict__ u, long long ldu,
-                                            double *__restrict__ part, int *err)
-{
-    double acc[RPL][NR];
-#pragma unroll
-    for (int k = 0; k < RPL; ++k)
-#pragma unroll
-        for (int r = 0; r < NR; ++r) acc[k][r] = 0.0;
-    const int cols = K.cols, ld = K.ld;
-    for (int e = T.e0; e < T.e1; ++e) {
-        const int sg = K.col[e];
-        const long long bi = K.blk[e];
-        // stage x_sigma as xs[j * NR + r]
-        if (K.is_near) {
-            int s3[3] = {0, 0, 0};
-            const int nl1 = 1 << nl_level;
-            for (int k = 0; k < d; ++k) s3[k] = (sg >> (nl_level * k)) & (nl1 - 1);
-            for (int j = lane; j < cols; j += 32) {
-                int jj = j;
-                long long nat = 0, str = 1;
-                for (int k = 0; k < d; ++k) {
-                    nat += (long long)(s3[k] * leaf + jj % leaf) * str;
-                    jj /= leaf;
-                    str *= n;
-                }
-#pragma unroll
-                for (int r = 0; r < NR; ++r) xs[j * NR + r] = u[nat + ldu * r];
-            }
-        } else {
-            const double *xb = K.x + (long long)sg * K.x_box_stride;
-            for (int j = lane; j < cols; j += 32)
-#pragma unroll
-                for (int r = 0; r < NR; ++r) xs[j * NR + r] = xb[(long long)r * cols + j];
-        }
-        __syncwarp();
-        const double *__restrict__ G = K.blocks + bi * K.blk_stride + lane;
-        int s = 0;
-        for (; s + 4 <= cols; s += 4) {
-            double g[4][RPL];
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-#pragma unroll
-                for (int k = 0; k < RPL; ++k) g[q][k] = ldblk<CS>(G + (long long)(s + q) * ld + 32 * k);
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-#pragma unroll
-                for (int r = 0; r < NR; ++r) {
-                    const double xv = xs[(s + q) * NR + r];
-#pragma unroll
-                    for (int k = 0; k < RPL; ++k) acc[k][r] = fma(g[q][k], xv, acc[k][r]);
-                }
-        }
-        for (; s < cols; ++s) {
-#pragma unroll
-            for (int r = 0; r < NR; ++r) {
-                const double xv = xs[s * NR + r];
-#pragma unroll
-                for (int k = 0; k < RPL; ++k)
-                    acc[k][r] = fma(ldblk<CS>(G + (long long)s * ld + 32 * k), xv, acc[k][r]);
-            }
-        }
-        __syncwarp();
-    }
-    double *out = part + T.part;
-#pragma unroll
-    for (int r = 0; r < NR; ++r)
-#pragma unroll
-        for (int k = 0; k < RPL; ++k) out[(long long)r * ld + lane + 32 * k] = acc[k][r];
-}
-
-template <int NR, bool CS>
-__global__ void __launch_bounds__(256) stream_kernel(const Task *__restrict__ tasks, int ntasks,
-                                                     const KindDesc *__restrict__ kinds, int d,
-                                                     int n, int leaf, int nl_level,
-                                                     const double *__restrict__ u, long long ldu,
-                                                     int max_cols, double *__restrict__ part,
-                                                     int *err)
-{
-    extern __shared__ double sm[];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    double *xs = sm + (long long)wib * max_cols * NR;
-    const int wpb = blockDim.x >> 5;
-    for (int t = blockIdx.x * wpb + wib; t < ntasks; t += gridDim.x * wpb) {
-        const Task T = tasks[t];
-        const KindDesc K = kinds[T.kind];
-        switch (K.rpl) {
-#define HTLR_RPL_CASE(R)                                                                   \
-    case R: stream_task<R, NR, CS>(T, K, lane, xs, d, n, leaf, nl_level, u, ldu, part, err); break;
-            HTLR_RPL_CASE(1) HTLR_RPL_CASE(2) HTLR_RPL_CASE(3) HTLR_RPL_CASE(4)
-            HTLR_RPL_CASE(5) HTLR_RPL_CASE(6) HTLR_RPL_CASE(7) HTLR_RPL_CASE(8)
-            HTLR_RPL_CASE(9) HTLR_RPL_CASE(10) HTLR_RPL_CASE(11) HTLR_RPL_CASE(12)
-            HTLR_RPL_CASE(13) HTLR_RPL_CASE(14) HTLR_RPL_CASE(15) HTLR_RPL_CASE(16)
-#undef HTLR_RPL_CASE
-        default:
-            if (lane == 0) atomicExch(err, (int)kDevBadTask);
-        }
+    switch (prec) {
+    case kPrecDF64: launch_stream_df64(a); break;
+    case kPrecFP32: launch_stream_fp32(a); break;
+    default: launch_stream_fp64(a); break;
     }
 }
 
-template <int NR, bool CS>
-static void launch_stream_t(const Task *d_tasks, int ntasks, const KindDesc *d_kinds, int d,
-                            int n, int leaf, int nl_level, const double *u, long long ldu,
-                            int max_cols, double *d_part, int *d_err, int blocks, int threads,
-                            size_t smem, cudaStream_t s)
+int leaf_level(int n, int leaf)
 {
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(stream_kernel<NR, CS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-    stream_kernel<NR, CS><<<blocks, threads, smem, s>>>(d_tasks, ntasks, d_kinds, d, n, leaf,
-                                                        nl_level, u, ldu, max_cols, d_part, d_err);
-}
-
-void launch_stream(const Task *d_tasks, int ntasks, const KindDesc *d_kinds, int max_rpl, int d,
-                   int n, int leaf, const double *u, long long ldu, int nrhs_here, int max_cols,
-                   double *d_part, int *d_err, bool streaming, cudaStream_t s)
-{
-    (void)max_rpl;
-    if (ntasks <= 0) return;
-    int nl_level = 0;
-    while ((leaf << nl_level) < n) ++nl_level;
-    const int threads = 256, wpb = threads / 32;
-    int blocks = (ntasks + wpb - 1) / wpb;
-    const int cap = 152 * 8;
-    if (blocks > cap) blocks = cap;
-    size_t smem = sizeof(double) * (size_t)wpb * max_cols * nrhs_here;
-#define HTLR_NR_CASE(R)                                                                        \
-    case R:                                                                                    \
-        if (streaming)                                                                         \
-            launch_stream_t<R, true>(d_tasks, ntasks, d_kinds, d, n, leaf, nl_level, u, ldu,   \
-                                     max_cols, d_part, d_err, blocks, threads, smem, s);       \
-        else                                                                                   \
-            launch_stream_t<R, false>(d_tasks, ntasks, d_kinds, d, n, leaf, nl_level, u, ldu,  \
-                                      max_cols, d_part, d_err, blocks, threads, smem, s);      \
-        break;
-    switch (nrhs_here) {
-        HTLR_NR_CASE(1) HTLR_NR_CASE(2) HTLR_NR_CASE(3) HTLR_NR_CASE(4)
-    default: break;
-    }
-#undef HTLR_NR_CASE
+    int l = 0;
+    while ((leaf << l) < n) ++l;
+    return l;
 }
 
 // ---------------------------------------------------------------------------------

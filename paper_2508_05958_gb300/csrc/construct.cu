@@ -256,6 +256,38 @@ void launch_cores(const KernelDesc &k, int d, int p, int pe, int ld, int apply_r
 }
 
 // ---------------------------------------------------------------------------------
+// Precision conversions of finished blocks.
+// df64: x = hi + lo with hi = fl32(x), lo = fl32(x - hi); the pair overwrites x in place.
+// ---------------------------------------------------------------------------------
+__global__ void split_df64_kernel(double *buf, size_t count)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
+         i += (size_t)gridDim.x * blockDim.x) {
+        double x = buf[i];
+        float h = __double2float_rn(x);
+        float l = __double2float_rn(x - (double)h);
+        reinterpret_cast<float2 *>(buf)[i] = make_float2(h, l);
+    }
+}
+
+__global__ void to_fp32_kernel(const double *src, float *dst, size_t count)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
+         i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = __double2float_rn(src[i]);
+}
+
+void launch_split_df64(double *d_buf, size_t count, cudaStream_t s)
+{
+    if (count) split_df64_kernel<<<152 * 8, 256, 0, s>>>(d_buf, count);
+}
+
+void launch_to_fp32(const double *d_src, float *d_dst, size_t count, cudaStream_t s)
+{
+    if (count) to_fp32_kernel<<<152 * 8, 256, 0, s>>>(d_src, d_dst, count);
+}
+
+// ---------------------------------------------------------------------------------
 // Dense inadmissible leaves (eq. (4.1)): A_ij = a(x_i) delta_ij + K_ij h^d, with the
 // diagonal K_ii h^d from the quadrature above.  Leaf-local lexicographic indices,
 // column-major [j][i] with leading dimension ld.

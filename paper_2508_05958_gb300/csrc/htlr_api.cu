@@ -302,7 +302,7 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
     for (int lv = 1; lv <= L; ++lv) {
         LevelData &Lv = H->lev[lv];
         if (Lv.nfar == 0) continue;
-        size_t blk = (size_t)Lv.ld * Lv.pd * sizeof(double);
+        size_t blk = (size_t)Lv.ld * Lv.pd * prec_bytes(H->far_prec);
         auto ct = count_tasks(Lv.far_rowptr, Lv.nbox, blk);
         ntasks += ct.first;
         part_doubles += ct.first * (long long)H->nrc * Lv.ld;
@@ -318,7 +318,7 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
         }
     }
     {
-        size_t blk = (size_t)H->near_ld * rows_leaf * sizeof(double);
+        size_t blk = (size_t)H->near_ld * rows_leaf * prec_bytes(H->near_prec);
         auto ct = count_tasks(H->near_rowptr, 1 << (d * L), blk);
         ntasks += ct.first;
         part_doubles += ct.first * (long long)H->nrc * H->near_ld;
@@ -392,10 +392,33 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
         int *d_offs = nullptr;
         if (tmp.alloc(&d_offs, offs.size())) return HTLR_ECUDA;
         HTLR_CK(cudaMemcpyAsync(d_offs, offs.data(), sizeof(int) * offs.size(), cudaMemcpyHostToDevice, s));
-        if (dalloc(H, &Lv.d_cores, (size_t)Lv.ncores * Lv.ld * Lv.pd)) return HTLR_ECUDA;
-        launch_cores(H->kern, d, p, Lv.pe, Lv.ld, H->orth, side, H->wgt, Lv.d_R, Lv.ncores, d_offs,
-                     Lv.d_cores, d_scratch, nscr, s);
-        HTLR_CK(cudaGetLastError());
+        {
+            // cores are formed in FP64, then kept as FP64, split in place into (hi, lo)
+            // float pairs (df64), or converted to FP32
+            const size_t nel = (size_t)Lv.ncores * Lv.ld * Lv.pd;
+            double *dcore = nullptr;
+            if (H->far_prec == kPrecFP32) {
+                HTLR_CK(cudaMalloc(&dcore, nel * sizeof(double)));
+            } else if (dalloc(H, &dcore, nel)) {
+                return HTLR_ECUDA;
+            }
+            launch_cores(H->kern, d, p, Lv.pe, Lv.ld, H->orth, side, H->wgt, Lv.d_R, Lv.ncores,
+                         d_offs, dcore, d_scratch, nscr, s);
+            HTLR_CK(cudaGetLastError());
+            Lv.d_cores = dcore;
+            if (H->far_prec == kPrecDF64) launch_split_df64(dcore, nel, s);
+            if (H->far_prec == kPrecFP32) {
+                float *f32 = nullptr;
+                int rc2 = dalloc(H, &f32, nel);
+                if (rc2 == HTLR_OK) launch_to_fp32(dcore, f32, nel, s);
+                cudaError_t e2 = cudaStreamSynchronize(s);
+                cudaFree(dcore);
+                if (rc2) return rc2;
+                HTLR_CK(e2);
+                Lv.d_cores = f32;
+            }
+            HTLR_CK(cudaGetLastError());
+        }
         // lists
         if (dalloc(H, &Lv.d_far_col, Lv.nfar) || dalloc(H, &Lv.d_far_core, Lv.nfar) ||
             dalloc(H, &Lv.d_W, (size_t)Lv.nbox * H->nrc * Lv.pd) ||
@@ -441,12 +464,31 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
         if (!taus.empty())
             HTLR_CK(cudaMemcpyAsync(d_taus, taus.data(), sizeof(int) * taus.size(),
                                     cudaMemcpyHostToDevice, s));
-        if (dalloc(H, &H->d_near, (size_t)H->nnear_unique * H->near_ld * rows_leaf) ||
-            dalloc(H, &H->d_near_col, H->nnear) || dalloc(H, &H->d_near_blk, H->nnear))
+        if (dalloc(H, &H->d_near_col, H->nnear) || dalloc(H, &H->d_near_blk, H->nnear))
             return HTLR_ECUDA;
+        const size_t nel = (size_t)H->nnear_unique * H->near_ld * rows_leaf;
+        double *dnear = nullptr;
+        if (H->near_prec == kPrecFP32) {
+            HTLR_CK(cudaMalloc(&dnear, nel * sizeof(double)));
+        } else if (dalloc(H, &dnear, nel)) {
+            return HTLR_ECUDA;
+        }
         launch_near(H->kern, d, n, leaf, H->near_ld, H->h, H->wgt, H->diag,
                     stored ? H->d_a : nullptr, H->nnear_unique, d_offs, stored ? d_taus : nullptr,
-                    H->d_near, s);
+                    dnear, s);
+        HTLR_CK(cudaGetLastError());
+        H->d_near = dnear;
+        if (H->near_prec == kPrecDF64) launch_split_df64(dnear, nel, s);
+        if (H->near_prec == kPrecFP32) {
+            float *f32 = nullptr;
+            int rc2 = dalloc(H, &f32, nel);
+            if (rc2 == HTLR_OK) launch_to_fp32(dnear, f32, nel, s);
+            cudaError_t e2 = cudaStreamSynchronize(s);
+            cudaFree(dnear);
+            if (rc2) return rc2;
+            HTLR_CK(e2);
+            H->d_near = f32;
+        }
         HTLR_CK(cudaGetLastError());
         HTLR_CK(cudaMemcpyAsync(H->d_near_col, H->near_col.data(), sizeof(int) * H->nnear,
                                 cudaMemcpyHostToDevice, s));
@@ -482,13 +524,14 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
     for (int lv = 1; lv <= L; ++lv) {
         LevelData &Lv = H->lev[lv];
         if (Lv.nfar == 0) continue;
-        make_tasks(lv, Lv.far_rowptr, Lv.nbox, (size_t)Lv.ld * Lv.pd * sizeof(double), Lv.ld,
-                   Lv.row_task_begin);
+        make_tasks(lv, Lv.far_rowptr, Lv.nbox, (size_t)Lv.ld * Lv.pd * prec_bytes(H->far_prec),
+                   Lv.ld, Lv.row_task_begin);
         KindDesc &K = H->kinds[lv];
         K.col = Lv.d_far_col;
         K.blk = Lv.d_far_core;
         K.blocks = Lv.d_cores;
         K.blk_stride = (long long)Lv.ld * Lv.pd;
+        K.prec = H->far_prec;
         K.ld = Lv.ld;
         K.rows = Lv.pd;
         K.cols = Lv.pd;
@@ -502,13 +545,16 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
                                 sizeof(int) * Lv.row_task_begin.size(), cudaMemcpyHostToDevice, s));
     }
     {
+        H->near_task0 = (int)H->tasks.size();
         make_tasks(L + 1, H->near_rowptr, 1 << (d * L),
-                   (size_t)H->near_ld * rows_leaf * sizeof(double), H->near_ld, H->near_row_task);
+                   (size_t)H->near_ld * rows_leaf * prec_bytes(H->near_prec), H->near_ld,
+                   H->near_row_task);
         KindDesc &K = H->kinds[L + 1];
         K.col = H->d_near_col;
         K.blk = H->d_near_blk;
         K.blocks = H->d_near;
         K.blk_stride = (long long)H->near_ld * rows_leaf;
+        K.prec = H->near_prec;
         K.ld = H->near_ld;
         K.rows = rows_leaf;
         K.cols = rows_leaf;
@@ -559,6 +605,8 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
     st.bytes_work = sz.work + sz.lists;
     st.bytes_total = sz.total();
     st.diag_value = H->diag;
+    st.far_precision = H->far_prec;
+    st.near_precision = H->near_prec;
     return HTLR_OK;
 }
 
@@ -586,6 +634,42 @@ struct StageEvents {
 };
 
 bool handle_is_live(const htlr_handle *H) { return is_live(H); }
+
+// The block stream of one RHS chunk: one launch when far and near blocks share a
+// precision, else one launch per part.  Returns the number of launches.
+int launch_streams(const htlr_handle *H, const KindDesc *d_kinds, const double *u, long long ldu,
+                   int nh, double *part, cudaStream_t s)
+{
+    StreamArgs a;
+    a.tasks = H->d_tasks;
+    a.kinds = d_kinds;
+    a.d = H->d;
+    a.n = H->n;
+    a.leaf = H->leaf;
+    a.nl_level = leaf_level(H->n, H->leaf);
+    a.u = u;
+    a.ldu = ldu;
+    a.nrhs = nh;
+    a.max_cols = H->max_cols;
+    a.part = part;
+    a.err = H->d_err;
+    a.streaming = H->storage == HTLR_STORE_STORED;
+    a.stream = s;
+    const int nt = (int)H->tasks.size();
+    if (H->far_prec == H->near_prec) {
+        a.t0 = 0;
+        a.t1 = nt;
+        launch_stream(H->far_prec, a);
+        return 1;
+    }
+    a.t0 = 0;
+    a.t1 = H->near_task0;
+    launch_stream(H->far_prec, a);
+    a.t0 = H->near_task0;
+    a.t1 = nt;
+    launch_stream(H->near_prec, a);
+    return 2;
+}
 
 static int enqueue_matvec(const htlr_handle *H, const double *u, double *f, int nrhs,
                           StageEvents *tev = nullptr)
@@ -623,9 +707,8 @@ static int enqueue_matvec(const htlr_handle *H, const double *u, double *f, int 
         }
         mark(1);
         mark(2);
-        launch_stream(H->d_tasks, (int)H->tasks.size(), H->d_kinds, 16, d, n, H->leaf, uc, N, nh,
-                      H->max_cols, H->d_part, H->d_err, H->storage == HTLR_STORE_STORED, s);
-        ++launches;
+        launches += launch_streams(H, H->d_kinds, uc, N, nh, H->d_part, s);
+        
         mark(3);
         mark(4);
         for (int lv = 1; lv <= L; ++lv) {
@@ -686,6 +769,9 @@ int htlr_construct_ex(htlr_handle **out, const htlr_kernel *k, int d, int n, con
     int q = (o && o->quad_order > 0) ? o->quad_order : 16;
     if (q > 64) return fail(HTLR_EINVAL, "quad_order must be in 1..64");
     if (o && (o->orth < -1 || o->orth > 1)) return fail(HTLR_EINVAL, "orth must be -1, 0 or 1");
+    if (o && (o->far_precision < 0 || o->far_precision > 2 || o->near_precision < 0 ||
+              o->near_precision > 2))
+        return fail(HTLR_EINVAL, "precisions must be HTLR_PREC_FP64, _DF64 or _FP32");
 
     htlr_handle *H = nullptr;
     try {
@@ -705,6 +791,8 @@ int htlr_construct_ex(htlr_handle **out, const htlr_kernel *k, int d, int n, con
     H->eta = eta;
     H->q = q;
     H->orth = (o && o->orth == 0) ? 0 : 1;
+    H->far_prec = o ? o->far_precision : kPrecFP64;
+    H->near_prec = o ? o->near_precision : kPrecFP64;
     int rc;
     try {
         rc = build(H, grid, o);

@@ -32,6 +32,12 @@ constexpr int kMaxP = 16;
 // Device error codes written into the handle's error word.
 enum DevErr : int { kDevOk = 0, kDevBadIndex = 1, kDevBadTask = 2 };
 
+// Arithmetic of a block list (same values as the public htlr_precision enum).
+enum Prec : int { kPrecFP64 = 0, kPrecDF64 = 1, kPrecFP32 = 2 };
+
+// Bytes of one block element in memory for a precision.
+inline size_t prec_bytes(int prec) { return prec == kPrecFP32 ? 4 : 8; }
+
 struct KernelDesc {
     int type;
     double scale;
@@ -51,8 +57,9 @@ struct Task {
 struct KindDesc {
     const int *col;      // source box per entry
     const int *blk;      // block (core / dense) index per entry
-    const double *blocks;
-    long long blk_stride;  // doubles between consecutive blocks (ld * cols)
+    const void *blocks;  // double, float2 (hi, lo) or float elements, per `prec`
+    long long blk_stride;  // elements between consecutive blocks (ld * cols)
+    int prec;            // Prec of the blocks
     int ld;              // padded rows of a block
     int rows;            // real rows (pd_out)
     int cols;            // pd_in
@@ -69,7 +76,7 @@ struct LevelData {
     int *d_far_rowptr = nullptr, *d_far_col = nullptr, *d_far_core = nullptr;
     double *d_F = nullptr;      // nb x pe
     double *d_R = nullptr;      // pe x p
-    double *d_cores = nullptr;  // ncores x (ld * pd)
+    void *d_cores = nullptr;    // ncores x (ld * pd) elements of the far precision
     int64_t ncores = 0;
     double *d_W = nullptr, *d_H = nullptr;  // nbox x nrc x pd
     int task0 = 0, task1 = 0;               // task range (far) of this level
@@ -98,7 +105,7 @@ struct htlr_handle {
     int64_t nnear = 0, nnear_unique = 0;
     std::vector<int> near_rowptr, near_col, near_blk;
     int *d_near_rowptr = nullptr, *d_near_col = nullptr, *d_near_blk = nullptr;
-    double *d_near = nullptr;
+    void *d_near = nullptr;     // dense blocks, elements of the near precision
     int near_ld = 0, near_rows = 0;
     std::vector<int> near_row_task;  // per leaf: first task, size nleaf + 1
     int *d_near_row_task = nullptr;
@@ -110,6 +117,8 @@ struct htlr_handle {
     double *d_part = nullptr;
     long long part_doubles = 0;
     int max_cols = 1;
+    int far_prec = 0, near_prec = 0;
+    int near_task0 = 0;  // first task of the inadmissible leaves
     int *d_err = nullptr;
     // host staging for htlr_matvec_host
     double *d_stage_u = nullptr, *d_stage_f = nullptr;
@@ -146,6 +155,10 @@ void launch_diag(const KernelDesc &k, int d, double h, int q, const double *d_gx
 void launch_cores(const KernelDesc &k, int d, int p, int pe, int ld, int apply_r, double side,
                   double wgt, const double *d_R, int64_t ncores, const int *d_off,
                   double *d_cores, double *d_scratch, int nscratch_ctas, cudaStream_t s);
+// Precision conversions of finished blocks: in place to (hi, lo) float pairs, or into a
+// separate FP32 array.
+void launch_split_df64(double *d_buf, size_t count, cudaStream_t s);
+void launch_to_fp32(const double *d_src, float *d_dst, size_t count, cudaStream_t s);
 // Dense blocks of inadmissible leaves: block b between leaves with offset d_off[b*3..]
 // (tau - sigma) and, for STORED, target leaf d_tau[b] (to add a on the diagonal).
 void launch_near(const KernelDesc &k, int d, int n, int leaf, int ld, double h, double wgt,
@@ -155,10 +168,28 @@ void launch_near(const KernelDesc &k, int d, int n, int leaf, int ld, double h, 
 // ---- apply.cu -------------------------------------------------------------------
 void launch_up(int d, int n, int level, int nb, int pe, const double *d_F, const double *u,
                int nrhs_here, long long ldu, int nrc, double *d_W, cudaStream_t s);
+// Arguments of one launch of the block stream over tasks [t0, t1), all of one precision.
 // streaming = true marks the blocks as read once per matvec (evict-first loads).
-void launch_stream(const Task *d_tasks, int ntasks, const KindDesc *d_kinds, int max_rpl,
-                   int d, int n, int leaf, const double *u, long long ldu, int nrhs_here,
-                   int max_cols, double *d_part, int *d_err, bool streaming, cudaStream_t s);
+struct StreamArgs {
+    const Task *tasks;
+    int t0, t1;
+    const KindDesc *kinds;
+    int d, n, leaf, nl_level;
+    const double *u;
+    long long ldu;
+    int nrhs;
+    int max_cols;
+    double *part;
+    int *err;
+    bool streaming;
+    cudaStream_t stream;
+};
+void launch_stream_fp64(const StreamArgs &a);
+void launch_stream_df64(const StreamArgs &a);
+void launch_stream_fp32(const StreamArgs &a);
+void launch_stream(int prec, const StreamArgs &a);
+// Level of the leaves: n = leaf * 2^nl_level.
+int leaf_level(int n, int leaf);
 void launch_reduce_far(int nbox, int pd, int ld, int nrc, int nrhs_here, const int *d_row_task,
                        const Task *d_tasks, const double *d_part, double *d_H, cudaStream_t s);
 struct DownLevel {

@@ -57,6 +57,8 @@ size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 }  // namespace
 
 bool handle_is_live(const htlr_handle *H);
+int launch_streams(const htlr_handle *H, const KindDesc *d_kinds, const double *u, long long ldu,
+                   int nh, double *part, cudaStream_t s);
 
 int matvec_noalloc(const htlr_handle *H, const double *u, double *f, int nrhs)
 {
@@ -130,8 +132,7 @@ int matvec_noalloc(const htlr_handle *H, const double *u, double *f, int nrhs)
             launch_up(d, n, lv, Lv.nb, Lv.pe, Lv.d_F, uc, nh, N, H->nrc,
                       reinterpret_cast<double *>(base + w_off[lv]), s);
         }
-        launch_stream(H->d_tasks, (int)H->tasks.size(), d_kinds, 16, d, n, H->leaf, uc, N, nh,
-                      H->max_cols, part, H->d_err, H->storage == HTLR_STORE_STORED, s);
+        launch_streams(H, d_kinds, uc, N, nh, part, s);
         for (int lv = 1; lv <= L; ++lv) {
             const LevelData &Lv = H->lev[lv];
             if (Lv.nfar == 0) continue;

@@ -18,6 +18,7 @@ HTLR_OK, HTLR_EINVAL, HTLR_ENOMEM, HTLR_ECUDA, HTLR_EUNSUPPORTED, HTLR_ETIMEOUT,
 K_LOG, K_INV_R, K_EXP_R, K_GAUSS, K_POLY, K_CONST = range(6)
 GRID_UNIFORM, GRID_TENSOR = 0, 1
 STORE_AUTO, STORE_STORED, STORE_SHARED = 0, 1, 2
+PREC_FP64, PREC_DF64, PREC_FP32 = 0, 1, 2
 MAX_LEVELS = 16
 
 NUM_STAGES = 4
@@ -44,7 +45,8 @@ class htlr_grid(ctypes.Structure):
 
 class htlr_options(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int), ("orth", ctypes.c_int), ("quad_order", ctypes.c_int),
-                ("stream", ctypes.c_void_p), ("hbm_limit", ctypes.c_size_t)]
+                ("stream", ctypes.c_void_p), ("hbm_limit", ctypes.c_size_t),
+                ("far_precision", ctypes.c_int), ("near_precision", ctypes.c_int)]
 
 
 class htlr_stats(ctypes.Structure):
@@ -55,7 +57,8 @@ class htlr_stats(ctypes.Structure):
                 ("paper_storage_doubles", ctypes.c_double), ("bytes_cores", ctypes.c_size_t),
                 ("bytes_near", ctypes.c_size_t), ("bytes_factors", ctypes.c_size_t),
                 ("bytes_work", ctypes.c_size_t), ("bytes_total", ctypes.c_size_t),
-                ("diag_value", ctypes.c_double)]
+                ("diag_value", ctypes.c_double), ("far_precision", ctypes.c_int),
+                ("near_precision", ctypes.c_int)]
 
 
 _lock = threading.Lock()
@@ -136,7 +139,8 @@ def _hptr(a):
 
 
 def htlr_construct(ktype, d, n, leaf, r, eta, *, kscale=1.0, kparam=0.0, a=None, grid=None,
-                   storage=STORE_AUTO, orth=-1, quad_order=0, stream=None, hbm_limit=0):
+                   storage=STORE_AUTO, orth=-1, quad_order=0, stream=None, hbm_limit=0,
+                   far_precision=0, near_precision=0):
     """Construct (Algorithm 1).  ``a``: host array of N values (natural order) or None.
     ``grid``: None (uniform) or (coords (d, n), edges (d, n+1)).  Returns an opaque handle
     (int).  ``stream``: a torch.cuda.Stream, a raw cudaStream_t int, or None."""
@@ -156,7 +160,8 @@ def htlr_construct(ktype, d, n, leaf, r, eta, *, kscale=1.0, kparam=0.0, a=None,
         a = np.ascontiguousarray(a, dtype=np.float64)
         keep.append(a)
         g.a = _hptr(a)
-    o = htlr_options(storage, orth, quad_order, _stream_ptr(stream), hbm_limit)
+    o = htlr_options(storage, orth, quad_order, _stream_ptr(stream), hbm_limit, far_precision,
+                     near_precision)
     h = ctypes.c_void_p()
     _check(L.htlr_construct_ex(ctypes.byref(h), ctypes.byref(k), d, n, ctypes.byref(g), leaf, r,
                                eta, ctypes.byref(o)))

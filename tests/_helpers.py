@@ -3,7 +3,8 @@ import numpy as np
 
 
 def gpu_matvec(w, u=None, nrhs=None, storage=0, orth=-1, eta=None, ktype=None, kparam=None,
-               kscale=None, a="default", p=None, leaf=None, repeat=1, host=False):
+               kscale=None, a="default", p=None, leaf=None, repeat=1, host=False,
+               far_precision=0, near_precision=0):
     """Construct the HTLR operator of workload w on cuda:0 and apply it to u (N x nrhs
     column-major numpy).  Returns (f, info)."""
     import torch
@@ -16,7 +17,8 @@ def gpu_matvec(w, u=None, nrhs=None, storage=0, orth=-1, eta=None, ktype=None, k
                             w.eta if eta is None else eta,
                             kscale=w.kscale if kscale is None else kscale,
                             kparam=w.kparam if kparam is None else kparam, a=a,
-                            storage=storage, orth=orth)
+                            storage=storage, orth=orth, far_precision=far_precision,
+                            near_precision=near_precision)
     try:
         info = htlr.htlr_info(H)
         if host:

@@ -154,3 +154,45 @@ def test_memory_limit_refusal():
     with pytest.raises(htlr.HTLRError) as ei:
         htlr.htlr_construct(1, 3, 32, 4, 5, 1.0, storage=1, hbm_limit=1 << 20)
     assert ei.value.code == htlr.HTLR_ENOMEM
+
+
+# ----------------------------------------------------------------------------------
+# Precisions: df64 (FP64 accuracy through FP32 pairs) meets the FP64 tolerance; the FP32
+# far field meets the mixed-precision tolerance (1e-6 relative, stated for that mode).
+# ----------------------------------------------------------------------------------
+MIXED_TOL = 1e-6
+
+
+@pytest.mark.parametrize("storage", [1, 2])
+@pytest.mark.parametrize("name", ["c1", "c2"])
+def test_df64_meets_fp64_tolerance(oracle, name, storage):
+    from paper_2508_05958_gb300.workloads import workload
+    w = workload(name)
+    u = w.u(nrhs=2)
+    f, info = gpu_matvec(w, u, storage=storage, far_precision=1, near_precision=1)
+    assert info["far_precision"] == 1 and info["near_precision"] == 1
+    ref, _ = _oracle_htlr(oracle, w, u)
+    assert rel(f, ref) < TOL
+
+
+@pytest.mark.parametrize("near", [0, 1])
+@pytest.mark.parametrize("storage", [1, 2])
+def test_fp32_far_field_mixed_tolerance(oracle, near, storage):
+    from paper_2508_05958_gb300.workloads import workload
+    w = workload("c2")
+    u = w.u(nrhs=1)
+    f, info = gpu_matvec(w, u, storage=storage, far_precision=2, near_precision=near)
+    ref, _ = _oracle_htlr(oracle, w, u)
+    err = rel(f, ref)
+    assert err < MIXED_TOL, err
+    assert err > 1e-12                      # it is genuinely FP32 arithmetic
+
+
+def test_df64_polynomial_exactness_and_determinism(oracle):
+    from paper_2508_05958_gb300.workloads import Workload
+    w = Workload("poly", d=3, n=16, ktype=4, leaf=2, p=3, eta=1.0, kparam=2, a_kind="one", seed=22)
+    u = w.u(nrhs=3)
+    outs, _ = gpu_matvec(w, u, far_precision=1, near_precision=1, repeat=2)
+    assert np.array_equal(outs[0], outs[1])
+    fd = oracle.dense_rows(w.d, w.n, 4, u, param=2, a=w.a())
+    assert rel(outs[0], fd) < 1e-12
