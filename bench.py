@@ -287,7 +287,8 @@ def run_gpu(args, w):
     torch.cuda.synchronize()
     construct_s = time.perf_counter() - t0
     info = htlr.htlr_info(H)
-    storage_name = {1: "STORED", 2: "SHARED"}.get(info["storage"], "?") + " " + dtype_name(info)
+    storage_name = ({1: "STORED", 2: "SHARED", 3: "GENERATED"}.get(info["storage"], "?") + " " +
+                    dtype_name(info))
     nrhs = w.nrhs
     U = w.u(nrhs=nrhs)
     with torch.cuda.stream(stream):

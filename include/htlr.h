@@ -79,9 +79,13 @@ typedef enum {
     HTLR_STORE_AUTO = 0,    /* STORED if it fits the limit, else SHARED when allowed */
     HTLR_STORE_STORED = 1,  /* one core per admissible block and one dense matrix per
                                inadmissible block, as Algorithm 1 builds them */
-    HTLR_STORE_SHARED = 2   /* uniform grid + translation-invariant kernel: blocks with the
+    HTLR_STORE_SHARED = 2,  /* uniform grid + translation-invariant kernel: blocks with the
                                same level and box offset are equal, so one core (and one
                                dense block) per (level, offset) is kept */
+    HTLR_STORE_GENERATED = 3 /* cores per (level, offset) as SHARED; the inadmissible blocks
+                               are not stored but recomputed from the kernel function in
+                               every matvec.  Always used on tensor grids, whose dense
+                               blocks differ from pair to pair */
 } htlr_storage;
 
 /* Arithmetic of the far-field (core) and near-field (dense block) products. */

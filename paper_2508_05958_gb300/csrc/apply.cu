@@ -1,94 +1,121 @@
 // HMultVec (Algorithm 2) on the GPU, level-batched.
 //
 // Algorithm 2 applies each admissible block (tau, sigma) as W = U_sigma x_l V_l^T,
-// H = G W, F = H x_l U_l (eq. (4.3)), and each inadmissible leaf as a dense gemv.  On a
-// uniform grid the factors of a level are the same for every box, so the source-side
-// contraction W_sigma depends on sigma alone and the target-side expansion is linear in
-// H_tau: the same sums are taken as
-//   up      W_sigma = u_sigma x_1 F^T ... x_d F^T        once per (level, box)
+// H = G W, F = H x_l U_l (eq. (4.3)), and each inadmissible leaf as a dense gemv.  The
+// factors of a box depend on that box alone (on a uniform grid they are even the same
+// for every box of a level), so the source-side contraction W_sigma is shared by every
+// block with source sigma and the target-side expansion is linear in H_tau; the same
+// sums are taken as
+//   up      W_sigma = u_sigma x_1 V_1^T ... x_d V_d^T    once per (level, box)
 //   stream  H_tau = sum_sigma G_{tau sigma} W_sigma     every admissible block
 //           f_tau = sum_sigma A_{tau sigma} u_sigma     every inadmissible leaf
-//   out     f_tau += sum_levels H_anc x_1 F ... x_d F   restricted to the leaf's rows
+//   out     f_tau += sum_levels H_anc x_1 U_1 ... x_d U_d  restricted to the leaf's rows
 // The stream step reads every core and dense block once; it is the hot loop.
 #include "htlr_internal.h"
 
 namespace htlr {
 
+struct BoxDims {
+    int first[3], cnt[3];
+    const double *U[3], *V[3];
+};
+
+__device__ __forceinline__ BoxDims box_dims(const LevelGeom &g, int d, int box)
+{
+    BoxDims b;
+    const int m = (1 << g.level) - 1;
+    for (int k = 0; k < 3; ++k) {
+        if (k < d) {
+            int bk = (box >> (g.level * k)) & m;
+            b.first[k] = g.first[k][bk];
+            b.cnt[k] = g.cnt[k][bk];
+            b.U[k] = g.Upool + g.uoff[k][bk];
+            b.V[k] = g.Vpool + g.voff[k][bk];
+        } else {
+            b.first[k] = 0;
+            b.cnt[k] = 1;
+            b.U[k] = b.V[k] = nullptr;
+        }
+    }
+    return b;
+}
+
 // ---------------------------------------------------------------------------------
 // up: one CTA per (box, rhs).  Mode products in the order 1, 2, (3), slab by slab of
 // the last dimension so that shared memory stays bounded for large boxes.
 // ---------------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) up_kernel(int d, int n, int level, int nb, int pe,
-                                                 const double *__restrict__ F,
+__global__ void __launch_bounds__(128) up_kernel(int d, int n, LevelGeom g,
                                                  const double *__restrict__ u, long long ldu,
                                                  int nrc, double *__restrict__ W, int slab)
 {
     extern __shared__ double sm[];
     const int box = blockIdx.x, r = blockIdx.y;
-    const int nb1 = 1 << level;
-    int b[3] = {0, 0, 0};
-    for (int k = 0; k < d; ++k) b[k] = (box >> (level * k)) & (nb1 - 1);
+    const int pe = g.pe, mc = g.maxcnt;
+    const BoxDims b = box_dims(g, d, box);
     const double *ur = u + ldu * r;
-    double *Fs = sm;                      // nb x pe
-    double *Y1 = Fs + nb * pe;            // pe x nb x slab  (mode-1 result of a slab)
-    double *Y2 = Y1 + pe * nb * slab;     // pe x pe x nb    (d = 3) or pe x pe (d = 2)
-    for (int i = threadIdx.x; i < nb * pe; i += blockDim.x) Fs[i] = F[i];
+    double *Vs = sm;                      // d factors, mc x pe each (leading dim cnt_k)
+    double *Y1 = Vs + 3 * mc * pe;        // pe x c2 x slab
+    double *Y2 = Y1 + pe * mc * slab;     // pe x pe x c3
+    for (int k = 0; k < d; ++k)
+        for (int i = threadIdx.x; i < b.cnt[k] * pe; i += blockDim.x) Vs[k * mc * pe + i] = b.V[k][i];
     __syncthreads();
-    const int n3 = (d == 3) ? nb : 1;
-    const long long base = (long long)b[0] * nb + (long long)n * b[1] * nb +
-                           (d == 3 ? (long long)n * n * b[2] * nb : 0);
-    for (int i3g = 0; i3g < n3; i3g += slab) {
-        int ns = min(slab, n3 - i3g);
-        // mode 1 on the slab: Y1[mu1 + pe (i2 + nb j3)] = sum_i1 F[i1, mu1] u[i1, i2, i3]
-        for (int idx = threadIdx.x; idx < pe * nb * ns; idx += blockDim.x) {
+    const int c1 = b.cnt[0], c2 = b.cnt[1], c3 = (d == 3) ? b.cnt[2] : 1;
+    const double *V1 = Vs, *V2 = Vs + mc * pe, *V3 = Vs + 2 * mc * pe;
+    const long long base = (long long)b.first[0] + (long long)n * b.first[1] +
+                           (d == 3 ? (long long)n * n * b.first[2] : 0);
+    for (int i3g = 0; i3g < c3; i3g += slab) {
+        const int ns = min(slab, c3 - i3g);
+        // mode 1: Y1[mu1 + pe (i2 + c2 j3)] = sum_i1 V1[i1, mu1] u[i1, i2, i3]
+        for (int idx = threadIdx.x; idx < pe * c2 * ns; idx += blockDim.x) {
             int mu1 = idx % pe, rest = idx / pe;
-            int i2 = rest % nb, j3 = rest / nb;
+            int i2 = rest % c2, j3 = rest / c2;
             const double *row = ur + base + (long long)n * i2 + (long long)n * n * (i3g + j3);
             double acc = 0.0;
-            for (int i1 = 0; i1 < nb; ++i1) acc = fma(Fs[i1 + nb * mu1], row[i1], acc);
+            for (int i1 = 0; i1 < c1; ++i1) acc = fma(V1[i1 + c1 * mu1], row[i1], acc);
             Y1[idx] = acc;
         }
         __syncthreads();
-        // mode 2: Y2[mu1 + pe (mu2 + pe i3)] = sum_i2 F[i2, mu2] Y1[mu1 + pe (i2 + nb j3)]
+        // mode 2: Y2[mu1 + pe (mu2 + pe i3)] = sum_i2 V2[i2, mu2] Y1[mu1 + pe (i2 + c2 j3)]
         for (int idx = threadIdx.x; idx < pe * pe * ns; idx += blockDim.x) {
             int mu1 = idx % pe, rest = idx / pe;
             int mu2 = rest % pe, j3 = rest / pe;
             double acc = 0.0;
-            for (int i2 = 0; i2 < nb; ++i2)
-                acc = fma(Fs[i2 + nb * mu2], Y1[mu1 + pe * (i2 + nb * j3)], acc);
+            for (int i2 = 0; i2 < c2; ++i2)
+                acc = fma(V2[i2 + c2 * mu2], Y1[mu1 + pe * (i2 + c2 * j3)], acc);
             Y2[mu1 + pe * (mu2 + pe * (i3g + j3))] = acc;
         }
         __syncthreads();
     }
-    const int pd = (d == 3) ? pe * pe * pe : pe * pe;
+    const int pd = g.pd;
     double *Wout = W + ((long long)box * nrc + r) * pd;
     if (d == 2) {
         for (int idx = threadIdx.x; idx < pd; idx += blockDim.x) Wout[idx] = Y2[idx];
         return;
     }
-    // mode 3: W[mu1 + pe (mu2 + pe mu3)] = sum_i3 F[i3, mu3] Y2[mu1 + pe (mu2 + pe i3)]
+    // mode 3: W[mu1 + pe (mu2 + pe mu3)] = sum_i3 V3[i3, mu3] Y2[mu1 + pe (mu2 + pe i3)]
     for (int idx = threadIdx.x; idx < pd; idx += blockDim.x) {
         int m12 = idx % (pe * pe), mu3 = idx / (pe * pe);
         double acc = 0.0;
-        for (int i3 = 0; i3 < nb; ++i3) acc = fma(Fs[i3 + nb * mu3], Y2[m12 + pe * pe * i3], acc);
+        for (int i3 = 0; i3 < c3; ++i3) acc = fma(V3[i3 + c3 * mu3], Y2[m12 + pe * pe * i3], acc);
         Wout[idx] = acc;
     }
 }
 
-void launch_up(int d, int n, int level, int nb, int pe, const double *d_F, const double *u,
-               int nrhs_here, long long ldu, int nrc, double *d_W, cudaStream_t s)
+void launch_up(int d, int n, const LevelGeom &g, const double *u, int nrhs_here, long long ldu,
+               int nrc, double *d_W, cudaStream_t s)
 {
-    int nbox = 1 << (d * level);
-    int n3 = (d == 3) ? nb : 1;
-    // slab so that the mode-1 buffer stays within ~64 KB
+    const int nbox = 1 << (d * g.level);
+    const int mc = g.maxcnt, pe = g.pe;
+    const int n3 = (d == 3) ? mc : 1;
+    // slab of the last dimension so that the mode-1 buffer stays within 64 KB
     int slab = n3;
-    while (slab > 1 && (long long)pe * nb * slab > 8192) slab = (slab + 1) / 2;
-    size_t smem = sizeof(double) * ((size_t)nb * pe + (size_t)pe * nb * slab +
+    while (slab > 1 && (long long)pe * mc * slab > 8192) slab = (slab + 1) / 2;
+    size_t smem = sizeof(double) * ((size_t)3 * mc * pe + (size_t)pe * mc * slab +
                                     (size_t)pe * pe * n3);
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(up_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 grid(nbox, nrhs_here);
-    up_kernel<<<grid, 128, smem, s>>>(d, n, level, nb, pe, d_F, u, ldu, nrc, d_W, slab);
+    up_kernel<<<grid, 128, smem, s>>>(d, n, g, u, ldu, nrc, d_W, slab);
 }
 
 // The block stream (the hot loop) lives in stream_impl.cuh, instantiated per
@@ -142,136 +169,117 @@ void launch_reduce_far(int nbox, int pd, int ld, int nrc, int nrhs_here, const i
 }
 
 // ---------------------------------------------------------------------------------
-// out: one CTA per (leaf, rhs).  f_tau = (sum of the leaf's inadmissible-block partials)
-// [+ a u] + sum over the far levels of H_anc x_1 F x_2 F (x_3 F), F restricted to the
-// rows of the leaf inside its ancestor; written once, in natural order.
+// out: one CTA per (leaf, rhs).  f_tau = base + sum over the far levels of
+// H_anc x_1 U_1 x_2 U_2 (x_3 U_3), each U restricted to the rows of the leaf inside its
+// ancestor; written once, in natural order.  The base is the sum of the leaf's
+// dense-block partials in task order [+ a u], or the generated near field already in f.
 // ---------------------------------------------------------------------------------
-struct DownArgs {
-    int ndown;
-    DownLevel lv[HTLR_MAX_LEVELS];
-};
+constexpr int kOutPer = 8;  // rows per thread: leaves of up to 8 * 256 points
 
-__global__ void __launch_bounds__(256) out_kernel(int d, int n, int leaf, int L, int nrc,
-                                                  const int *__restrict__ near_row_task,
-                                                  const Task *__restrict__ tasks,
-                                                  const double *__restrict__ part, int near_ld,
-                                                  const double *__restrict__ a_add,
-                                                  const double *__restrict__ u, long long ldu,
-                                                  DownArgs down, double *__restrict__ f,
-                                                  long long ldf)
+__global__ void __launch_bounds__(256) out_kernel(OutArgs A)
 {
     extern __shared__ double sm[];
-    const int tau = blockIdx.x, r = blockIdx.y;
-    const int nl1 = 1 << L;
+    const int tau = blockIdx.x, r = blockIdx.y, d = A.d, n = A.n, L = A.L;
+    const BoxDims lb = box_dims(A.leafg, d, tau);
     int t3[3] = {0, 0, 0};
-    for (int k = 0; k < d; ++k) t3[k] = (tau >> (L * k)) & (nl1 - 1);
-    int rows = 1;
-    for (int k = 0; k < d; ++k) rows *= leaf;
-    // per-thread accumulators for rows i = threadIdx.x + blockDim.x * m
-    const int per = (rows + blockDim.x - 1) / blockDim.x;  // <= 8 (leaf^d <= 2048)
-    double acc[8];
-    long long nat[8];
-    for (int m = 0; m < per && m < 8; ++m) {
-        int i = threadIdx.x + blockDim.x * m;
+    for (int k = 0; k < d; ++k) t3[k] = (tau >> (L * k)) & ((1 << L) - 1);
+    const int rows = lb.cnt[0] * lb.cnt[1] * lb.cnt[2];
+    const int per = (rows + blockDim.x - 1) / blockDim.x;
+    double acc[kOutPer];
+    long long nat[kOutPer];
+    for (int m = 0; m < kOutPer; ++m) {
         acc[m] = 0.0;
         nat[m] = -1;
-        if (i < rows) {
-            int ii = i;
-            long long na = 0, str = 1;
-            for (int k = 0; k < d; ++k) {
-                na += (long long)(t3[k] * leaf + ii % leaf) * str;
-                ii /= leaf;
-                str *= n;
-            }
+        const int i = threadIdx.x + blockDim.x * m;
+        if (m < per && i < rows) {
+            const int j1 = i % lb.cnt[0], j23 = i / lb.cnt[0];
+            const int j2 = j23 % lb.cnt[1], j3 = j23 / lb.cnt[1];
+            const long long na = (long long)(lb.first[0] + j1) + (long long)n * (lb.first[1] + j2) +
+                                 (d == 3 ? (long long)n * n * (lb.first[2] + j3) : 0);
             nat[m] = na;
             double s = 0.0;
-            for (int k = near_row_task[tau]; k < near_row_task[tau + 1]; ++k)
-                s += part[tasks[k].part + (long long)r * near_ld + i];
-            if (a_add) s += a_add[na] * u[na + ldu * r];
+            if (A.near_in_f) {
+                s = A.f[na + A.ldf * r];
+            } else {
+                for (int k = A.near_row_task[tau]; k < A.near_row_task[tau + 1]; ++k)
+                    s += A.part[A.tasks[k].part + (long long)r * A.near_ld + i];
+                if (A.a_add) s += A.a_add[na] * A.u[na + A.ldu * r];
+            }
             acc[m] = s;
         }
     }
-    // far levels, in increasing level order
-    for (int q = 0; q < down.ndown; ++q) {
-        const DownLevel D = down.lv[q];
-        const int pe = D.pe, nb = D.nb, lev = D.level;
-        int anc = 0, o[3] = {0, 0, 0};
-        for (int k = 0; k < d; ++k) {
-            int ak = t3[k] >> (L - lev);
-            anc |= ak << (lev * k);
-            o[k] = (t3[k] - (ak << (L - lev))) * leaf;
-        }
-        const double *Hb = D.H + ((long long)anc * nrc + r) * D.pd;
+    for (int q = 0; q < A.ndown; ++q) {
+        const DownLevel &D = A.down[q];
+        const int pe = D.g.pe, lev = D.g.level;
+        int anc = 0;
+        for (int k = 0; k < d; ++k) anc |= (t3[k] >> (L - lev)) << (lev * k);
+        const BoxDims ab = box_dims(D.g, d, anc);
+        int o[3];
+        for (int k = 0; k < 3; ++k) o[k] = lb.first[k] - ab.first[k];
+        const int c1 = lb.cnt[0], c2 = lb.cnt[1], c3 = lb.cnt[2];
+        const int ca1 = ab.cnt[0], ca2 = ab.cnt[1], ca3 = ab.cnt[2];
+        const double *Hb = D.H + ((long long)anc * A.nrc + r) * D.g.pd;
         double *Hs = sm;                          // pd
-        double *Z3 = Hs + D.pd;                   // pe^2 * leaf   (d = 3)
-        double *Z2 = Z3 + pe * pe * leaf;         // pe * leaf^(d-1)
-        for (int i = threadIdx.x; i < D.pd; i += blockDim.x) Hs[i] = Hb[i];
+        double *Z3 = Hs + D.g.pd;                 // pe^2 * c3
+        double *Z2 = Z3 + pe * pe * c3;           // pe * c2 * c3
+        for (int i = threadIdx.x; i < D.g.pd; i += blockDim.x) Hs[i] = Hb[i];
         __syncthreads();
         const double *Zsrc = Hs;
         if (d == 3) {
-            // Z3[mu1 + pe (mu2 + pe j3)] = sum_mu3 F[o3 + j3, mu3] H[mu1 + pe (mu2 + pe mu3)]
-            for (int idx = threadIdx.x; idx < pe * pe * leaf; idx += blockDim.x) {
+            // Z3[mu1 + pe (mu2 + pe j3)] = sum_mu3 U3[o3 + j3, mu3] H[mu1 + pe (mu2 + pe mu3)]
+            for (int idx = threadIdx.x; idx < pe * pe * c3; idx += blockDim.x) {
                 int m12 = idx % (pe * pe), j3 = idx / (pe * pe);
                 double s = 0.0;
                 for (int m3 = 0; m3 < pe; ++m3)
-                    s = fma(D.F[o[2] + j3 + nb * m3], Hs[m12 + pe * pe * m3], s);
+                    s = fma(ab.U[2][o[2] + j3 + ca3 * m3], Hs[m12 + pe * pe * m3], s);
                 Z3[idx] = s;
             }
             __syncthreads();
             Zsrc = Z3;
         }
-        // Z2[mu1 + pe (j2 + leaf j3)] = sum_mu2 F[o2 + j2, mu2] Zsrc[mu1 + pe (mu2 + pe j3)]
-        const int n3 = (d == 3) ? leaf : 1;
-        for (int idx = threadIdx.x; idx < pe * leaf * n3; idx += blockDim.x) {
+        // Z2[mu1 + pe (j2 + c2 j3)] = sum_mu2 U2[o2 + j2, mu2] Zsrc[mu1 + pe (mu2 + pe j3)]
+        for (int idx = threadIdx.x; idx < pe * c2 * c3; idx += blockDim.x) {
             int mu1 = idx % pe, rest = idx / pe;
-            int j2 = rest % leaf, j3 = rest / leaf;
+            int j2 = rest % c2, j3 = rest / c2;
             double s = 0.0;
             for (int m2 = 0; m2 < pe; ++m2)
-                s = fma(D.F[o[1] + j2 + nb * m2], Zsrc[mu1 + pe * (m2 + pe * j3)], s);
+                s = fma(ab.U[1][o[1] + j2 + ca2 * m2], Zsrc[mu1 + pe * (m2 + pe * j3)], s);
             Z2[idx] = s;
         }
         __syncthreads();
-        for (int m = 0; m < per && m < 8; ++m) {
-            int i = threadIdx.x + blockDim.x * m;
-            if (i < rows) {
-                int j1 = i % leaf, j23 = i / leaf;
+        for (int m = 0; m < kOutPer; ++m) {
+            const int i = threadIdx.x + blockDim.x * m;
+            if (m < per && i < rows) {
+                int j1 = i % c1, j23 = i / c1;
                 double s = 0.0;
                 for (int m1 = 0; m1 < pe; ++m1)
-                    s = fma(D.F[o[0] + j1 + nb * m1], Z2[m1 + pe * j23], s);
+                    s = fma(ab.U[0][o[0] + j1 + ca1 * m1], Z2[m1 + pe * j23], s);
                 acc[m] += s;
             }
         }
         __syncthreads();
     }
-    for (int m = 0; m < per && m < 8; ++m)
-        if (nat[m] >= 0) f[nat[m] + ldf * r] = acc[m];
+    for (int m = 0; m < kOutPer; ++m)
+        if (nat[m] >= 0) A.f[nat[m] + A.ldf * r] = acc[m];
 }
 
-void launch_out(int d, int n, int leaf, int L, int nrc, int nrhs_here, const int *d_near_row_task,
-                const Task *d_tasks, const double *d_part, int near_ld, const double *d_a_add,
-                const double *u, long long ldu, const DownLevel *down, int ndown, double *f,
-                long long ldf, cudaStream_t s)
+void launch_out(const OutArgs &a, int max_rows, cudaStream_t s)
 {
-    DownArgs args;
-    args.ndown = ndown;
     size_t smem = 0;
-    for (int q = 0; q < ndown && q < HTLR_MAX_LEVELS; ++q) {
-        args.lv[q] = down[q];
-        int pe = down[q].pe;
-        size_t need = (size_t)down[q].pd + (size_t)pe * pe * leaf +
-                      (size_t)pe * leaf * (d == 3 ? leaf : 1);
+    const int mcl = a.leafg.maxcnt > 1 ? a.leafg.maxcnt : 1;  // largest leaf extent
+    for (int q = 0; q < a.ndown; ++q) {
+        const int pe = a.down[q].g.pe;
+        size_t need = (size_t)a.down[q].g.pd + (size_t)pe * pe * (a.d == 3 ? mcl : 1) +
+                      (size_t)pe * mcl * (a.d == 3 ? mcl : 1);
         if (need > smem) smem = need;
     }
     smem *= sizeof(double);
     if (smem == 0) smem = sizeof(double);
-    int rows = 1;
-    for (int k = 0; k < d; ++k) rows *= leaf;
-    int threads = rows < 256 ? ((rows + 31) / 32) * 32 : 256;
+    int threads = max_rows < 256 ? ((max_rows + 31) / 32) * 32 : 256;
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(out_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    dim3 grid(1 << (d * L), nrhs_here);
-    out_kernel<<<grid, threads, smem, s>>>(d, n, leaf, L, nrc, d_near_row_task, d_tasks, d_part,
-                                           near_ld, d_a_add, u, ldu, args, f, ldf);
+    dim3 grid(1 << (a.d * a.L), a.nrhs);
+    out_kernel<<<grid, threads, smem, s>>>(a);
 }
 
 }  // namespace htlr

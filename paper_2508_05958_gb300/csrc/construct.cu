@@ -352,4 +352,102 @@ void launch_near(const KernelDesc &k, int d, int n, int leaf, int ld, double h, 
                                         d_blocks);
 }
 
+// ---------------------------------------------------------------------------------
+// Tensor grids (§3.3 weights, Def. 3.3 tensor boxes): factors of every 1-D box of a
+// level.  U(i, mu) = L_mu(x_i) and V(i, mu) = L_mu(x_i) w_i on the Chebyshev points of
+// the box's geometric cell [k 2^-l, (k+1) 2^-l], barycentric form; w_i is the 1-D cell
+// width, so that the core needs no quadrature weight.  Grid (dimension, 1-D box).
+// ---------------------------------------------------------------------------------
+__global__ void factor_tensor_kernel(int n, int level, int p, const double *coords,
+                                     const double *width, const int *geo, double *Upool,
+                                     double *Vpool)
+{
+    const double pi = 3.141592653589793238462643;
+    const int l = blockIdx.y, k = blockIdx.x, nb1 = 1 << level;
+    const int *g = geo + (size_t)l * 4 * nb1;  // first, cnt, uoff, voff
+    const int first = g[k], cnt = g[nb1 + k], uo = g[2 * nb1 + k], vo = g[3 * nb1 + k];
+    const double side = ldexp(1.0, -level), lo = k * side;
+    for (int idx = threadIdx.x; idx < cnt * p; idx += blockDim.x) {
+        const int i = idx % cnt, mu = idx / cnt;
+        const double x = coords[(size_t)l * n + first + i];
+        double num = 0.0, den = 0.0;
+        int hit = -1;
+        for (int j = 0; j < p; ++j) {
+            double xj = lo + 0.5 * side * cos((2 * j + 1) * pi / (2.0 * p)) + 0.5 * side;
+            double wj = ((j & 1) ? -1.0 : 1.0) * sin((2 * j + 1) * pi / (2.0 * p));
+            double dx = x - xj;
+            if (dx == 0.0) hit = j;
+            double t = wj / dx;
+            den += t;
+            if (j == mu) num = t;
+        }
+        const double v = (hit >= 0) ? (hit == mu ? 1.0 : 0.0) : num / den;
+        Upool[uo + idx] = v;
+        Vpool[vo + idx] = v * width[(size_t)l * n + first + i];
+    }
+}
+
+void launch_factor_tensor(int d, int n, int level, int p, const double *coords,
+                          const double *width, const int *geo, double *Upool, double *Vpool,
+                          cudaStream_t s)
+{
+    dim3 grid(1 << level, d);
+    factor_tensor_kernel<<<grid, 128, 0, s>>>(n, level, p, coords, width, geo, Upool, Vpool);
+}
+
+// ---------------------------------------------------------------------------------
+// Tensor grids: K_ii w_i = int over the cell of point i of k(x_i, y) dy (eq. (1.4) with
+// the cell measure of §3.3), the cell split at x_i into 2^d boxes (of unequal sides when
+// x_i is off-centre), a q^d Gauss-Legendre rule on each.  One warp per point; lanes
+// split the nodes and a fixed shuffle tree reduces them.
+// ---------------------------------------------------------------------------------
+__global__ void diag_points_kernel(KernelDesc k, int d, int n, const double *coords,
+                                   const double *edges, int q, const double *gx,
+                                   const double *gw, double *diag)
+{
+    const long long N = (long long)n * n * (d == 3 ? n : 1);
+    const int lane = threadIdx.x & 31;
+    long long qd = 1;
+    for (int l = 0; l < d; ++l) qd *= q;
+    const long long total = qd << d;
+    for (long long i = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; i < N;
+         i += ((long long)gridDim.x * blockDim.x) >> 5) {
+        double x[3], a[3], b[3];
+        long long r = i;
+        for (int l = 0; l < d; ++l) {
+            int il = (int)(r % n);
+            r /= n;
+            x[l] = coords[(size_t)l * n + il];
+            a[l] = edges[(size_t)l * (n + 1) + il];
+            b[l] = edges[(size_t)l * (n + 1) + il + 1];
+        }
+        double acc = 0.0;
+        for (long long m = lane; m < total; m += 32) {
+            int c = (int)(m / qd);
+            long long rq = m % qd;
+            double disp[3], w = 1.0;
+            for (int l = 0; l < d; ++l) {
+                int kq = (int)(rq % q);
+                rq /= q;
+                double lo = ((c >> l) & 1) ? x[l] : a[l];
+                double hi = ((c >> l) & 1) ? b[l] : x[l];
+                double half = 0.5 * (hi - lo);
+                double y = 0.5 * (lo + hi) + half * gx[kq];
+                disp[l] = x[l] - y;
+                w *= half * gw[kq];
+            }
+            acc += w * kernel_of(k, d, disp);
+        }
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+        if (lane == 0) diag[i] = acc;
+    }
+}
+
+void launch_diag_points(const KernelDesc &k, int d, int n, const double *coords,
+                        const double *edges, int q, const double *gx, const double *gw,
+                        double *diag, cudaStream_t s)
+{
+    diag_points_kernel<<<152 * 16, 256, 0, s>>>(k, d, n, coords, edges, q, gx, gw, diag);
+}
+
 }  // namespace htlr

@@ -146,6 +146,62 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
         HTLR_CK(cudaMemcpyAsync(H->d_a, grid->a, sizeof(double) * N, cudaMemcpyHostToDevice, s));
     }
 
+    // ---- grid lines, cells and the 1-D boxes of every level (§2.2, Def. 3.3) ----
+    std::vector<double> xs((size_t)d * n), es((size_t)d * (n + 1)), ws((size_t)d * n);
+    for (int l = 0; l < d; ++l)
+        for (int i = 0; i <= n; ++i) {
+            if (H->tensor) {
+                es[(size_t)l * (n + 1) + i] = grid->edges[(size_t)l * (n + 1) + i];
+                if (i < n) xs[(size_t)l * n + i] = grid->coords[(size_t)l * n + i];
+            } else {
+                es[(size_t)l * (n + 1) + i] = i * H->h;
+                if (i < n) xs[(size_t)l * n + i] = (i + 0.5) * H->h;
+            }
+        }
+    for (int l = 0; l < d; ++l)
+        for (int i = 0; i < n; ++i)
+            ws[(size_t)l * n + i] = es[(size_t)l * (n + 1) + i + 1] - es[(size_t)l * (n + 1) + i];
+    if (dalloc(H, &H->d_coords, xs.size()) || dalloc(H, &H->d_edges, es.size()) ||
+        dalloc(H, &H->d_width, ws.size()))
+        return HTLR_ECUDA;
+    HTLR_CK(cudaMemcpyAsync(H->d_coords, xs.data(), sizeof(double) * xs.size(),
+                            cudaMemcpyHostToDevice, s));
+    HTLR_CK(cudaMemcpyAsync(H->d_edges, es.data(), sizeof(double) * es.size(),
+                            cudaMemcpyHostToDevice, s));
+    HTLR_CK(cudaMemcpyAsync(H->d_width, ws.data(), sizeof(double) * ws.size(),
+                            cudaMemcpyHostToDevice, s));
+    H->lev.assign(L + 1, LevelData());
+    for (int lv = 1; lv <= L; ++lv) {
+        LevelData &Lv = H->lev[lv];
+        const int nb1 = 1 << lv;
+        const double side = std::ldexp(1.0, -lv);
+        int maxc = 0;
+        for (int l = 0; l < d; ++l) {
+            Lv.first[l].assign(nb1, 0);
+            Lv.cnt[l].assign(nb1, 0);
+            // grid lines with coordinate in the half-open cell [k side, (k+1) side)
+            int i = 0;
+            for (int k = 0; k < nb1; ++k) {
+                const double hi = (k + 1) * side;
+                Lv.first[l][k] = i;
+                while (i < n && (xs[(size_t)l * n + i] < hi || k == nb1 - 1)) ++i;
+                Lv.cnt[l][k] = i - Lv.first[l][k];
+                if (Lv.cnt[l][k] < 1)
+                    return fail(HTLR_EINVAL, "a box of the cluster tree holds no grid line "
+                                             "(every node must be non-empty, Def. 2.1)");
+                maxc = std::max(maxc, Lv.cnt[l][k]);
+            }
+        }
+        Lv.maxcnt = maxc;
+    }
+    {
+        const LevelData &Ll = H->lev[L];
+        int rows = 1;
+        for (int l = 0; l < d; ++l) rows *= Ll.maxcnt;
+        H->max_leaf_rows = rows;
+    }
+    HTLR_CK(cudaStreamSynchronize(s));
+
     // ---- Nystrom diagonal (eq. (1.4)) ----
     {
         std::vector<double> gx, gw;
@@ -162,7 +218,6 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
     }
 
     // ---- block cluster tree walk (Def. 2.4), level by level ----
-    H->lev.assign(L + 1, LevelData());
     std::vector<int> prev_rowptr = {0, 1}, prev_col = {0};
     for (int lv = 1; lv <= L; ++lv) {
         LevelData &Lv = H->lev[lv];
@@ -218,11 +273,17 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
     H->nnear = (int64_t)H->near_col.size();
 
     // ---- per-level shapes and the storage decision ----
-    const int rows_leaf = ipow(leaf, d);
+    const int rows_leaf = ipow(leaf, d);  // uniform leaves (tensor leaves are ragged)
     H->near_rows = rows_leaf;
     H->near_ld = round_up(rows_leaf, 32);
-    if (H->near_ld / 32 > 16)
-        return fail(HTLR_EUNSUPPORTED, "leaf boxes above 512 points are not supported");
+    const int want0 = o ? o->storage : HTLR_STORE_AUTO;
+    H->near_generated = (H->tensor || want0 == HTLR_STORE_GENERATED) ? 1 : 0;
+    if (!H->near_generated && H->near_ld / 32 > 16)
+        return fail(HTLR_EUNSUPPORTED,
+                    "stored dense leaf blocks above 512 points are not supported (use "
+                    "HTLR_STORE_GENERATED)");
+    if (H->max_leaf_rows > 1024)
+        return fail(HTLR_EUNSUPPORTED, "leaf boxes above 1024 points are not supported");
     int first_far = -1;
     for (int lv = 1; lv <= L; ++lv) {
         LevelData &Lv = H->lev[lv];
@@ -308,7 +369,8 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
         part_doubles += ct.first * (long long)H->nrc * Lv.ld;
         sz_stored.cores += blk * Lv.nfar;
         sz_shared.cores += blk * shared_off[lv].size();
-        size_t fac = sizeof(double) * (2 * (size_t)Lv.nb * p + (size_t)p * p);
+        size_t fac = sizeof(double) * (H->tensor ? 2 * (size_t)d * n * p
+                                                 : 2 * (size_t)Lv.nb * p + (size_t)p * p);
         size_t work = 2 * sizeof(double) * (size_t)Lv.nbox * H->nrc * Lv.pd;
         size_t lists = sizeof(int) * (2 * (size_t)Lv.nfar + 2 * ((size_t)Lv.nbox + 1));
         for (Sizes *z : {&sz_stored, &sz_shared}) {
@@ -317,7 +379,16 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
             z->lists += lists;
         }
     }
-    {
+    if (H->near_generated) {
+        // no dense blocks: the per-point diagonal and the near lists only
+        sz_stored.near = sz_shared.near = sizeof(double) * (size_t)N;
+        size_t lists = sizeof(int) * ((size_t)H->nnear + (size_t)(1 << (d * L)) + 1);
+        size_t work = sizeof(double) * part_doubles + sizeof(Task) * ntasks;
+        for (Sizes *z : {&sz_stored, &sz_shared}) {
+            z->lists += lists;
+            z->work += work;
+        }
+    } else {
         size_t blk = (size_t)H->near_ld * rows_leaf * prec_bytes(H->near_prec);
         auto ct = count_tasks(H->near_rowptr, 1 << (d * L), blk);
         ntasks += ct.first;
@@ -338,9 +409,13 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
         limit = (size_t)(0.9 * (double)fr);
     }
     int want = o ? o->storage : HTLR_STORE_AUTO;
-    if (want == HTLR_STORE_AUTO) want = sz_stored.total() <= limit ? HTLR_STORE_STORED : HTLR_STORE_SHARED;
+    if (want == HTLR_STORE_GENERATED) want = HTLR_STORE_SHARED;  // cores per offset
+    if (want == HTLR_STORE_AUTO) {
+        if (H->tensor) want = HTLR_STORE_SHARED;
+        else want = sz_stored.total() <= limit ? HTLR_STORE_STORED : HTLR_STORE_SHARED;
+    }
     if (want != HTLR_STORE_STORED && want != HTLR_STORE_SHARED)
-        return fail(HTLR_EINVAL, "options.storage must be AUTO, STORED or SHARED");
+        return fail(HTLR_EINVAL, "options.storage must be AUTO, STORED, SHARED or GENERATED");
     const Sizes &sz = (want == HTLR_STORE_STORED) ? sz_stored : sz_shared;
     if (sz.total() > limit) {
         char buf[256];
@@ -357,14 +432,53 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
     int nscr = (int)std::max<long long>(1, std::min<long long>(2 * 152, (512ll << 20) / (8 * scratch_per)));
     double *d_scratch = nullptr;
     if (first_far >= 0 && tmp.alloc(&d_scratch, (size_t)nscr * scratch_per)) return HTLR_ECUDA;
+    // box geometry and factor offsets of every level (the leaf level is needed by the
+    // output and the generated near field even without admissible blocks)
+    for (int lv = 1; lv <= L; ++lv) {
+        LevelData &Lv = H->lev[lv];
+        const int nb1 = 1 << lv;
+        const int pe = Lv.nfar ? Lv.pe : p;
+        size_t pool = 0;
+        for (int l = 0; l < d; ++l) {
+            Lv.uoff[l].assign(nb1, 0);
+            Lv.voff[l].assign(nb1, 0);
+            if (H->tensor)
+                for (int k = 0; k < nb1; ++k) {
+                    Lv.uoff[l][k] = Lv.voff[l][k] = (int)pool;
+                    pool += (size_t)Lv.cnt[l][k] * pe;
+                }
+        }
+        std::vector<int> geo((size_t)d * 4 * nb1);
+        for (int l = 0; l < d; ++l)
+            for (int k = 0; k < nb1; ++k) {
+                geo[(size_t)l * 4 * nb1 + k] = Lv.first[l][k];
+                geo[(size_t)l * 4 * nb1 + nb1 + k] = Lv.cnt[l][k];
+                geo[(size_t)l * 4 * nb1 + 2 * nb1 + k] = Lv.uoff[l][k];
+                geo[(size_t)l * 4 * nb1 + 3 * nb1 + k] = Lv.voff[l][k];
+            }
+        if (dalloc(H, &Lv.d_geo, geo.size())) return HTLR_ECUDA;
+        HTLR_CK(cudaMemcpyAsync(Lv.d_geo, geo.data(), sizeof(int) * geo.size(),
+                                cudaMemcpyHostToDevice, s));
+        HTLR_CK(cudaStreamSynchronize(s));
+        if (Lv.nfar == 0) continue;
+        if (dalloc(H, &Lv.d_R, (size_t)p * p)) return HTLR_ECUDA;
+        const double side = std::ldexp(1.0, -lv);
+        if (H->tensor) {
+            // per-box factors; the cell widths sit in V (no orthogonalisation)
+            if (dalloc(H, &Lv.d_Upool, pool) || dalloc(H, &Lv.d_Vpool, pool)) return HTLR_ECUDA;
+            launch_factor_tensor(d, n, lv, p, H->d_coords, H->d_width, Lv.d_geo, Lv.d_Upool,
+                                 Lv.d_Vpool, s);
+        } else {
+            if (dalloc(H, &Lv.d_F, 2 * (size_t)Lv.nb * p)) return HTLR_ECUDA;
+            launch_factor(Lv.nb, p, Lv.pe, side, H->h, H->orth, Lv.d_F, Lv.d_R, s);
+            Lv.d_Upool = Lv.d_Vpool = Lv.d_F;
+        }
+        HTLR_CK(cudaGetLastError());
+    }
     for (int lv = 1; lv <= L; ++lv) {
         LevelData &Lv = H->lev[lv];
         if (Lv.nfar == 0) continue;
-        if (dalloc(H, &Lv.d_F, 2 * (size_t)Lv.nb * p) || dalloc(H, &Lv.d_R, (size_t)p * p))
-            return HTLR_ECUDA;
-        double side = std::ldexp(1.0, -lv);
-        launch_factor(Lv.nb, p, Lv.pe, side, H->h, H->orth, Lv.d_F, Lv.d_R, s);
-        HTLR_CK(cudaGetLastError());
+        const double side = std::ldexp(1.0, -lv);
         // core per block (STORED) or per offset (SHARED)
         std::vector<int> offs;
         if (stored) {
@@ -402,8 +516,10 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
             } else if (dalloc(H, &dcore, nel)) {
                 return HTLR_ECUDA;
             }
-            launch_cores(H->kern, d, p, Lv.pe, Lv.ld, H->orth, side, H->wgt, Lv.d_R, Lv.ncores,
-                         d_offs, dcore, d_scratch, nscr, s);
+            // uniform grid: the weight h^d multiplies the core (Algorithm 1); tensor grid:
+            // the cell widths are already in V
+            launch_cores(H->kern, d, p, Lv.pe, Lv.ld, H->orth, side, H->tensor ? 1.0 : H->wgt,
+                         Lv.d_R, Lv.ncores, d_offs, dcore, d_scratch, nscr, s);
             HTLR_CK(cudaGetLastError());
             Lv.d_cores = dcore;
             if (H->far_prec == kPrecDF64) launch_split_df64(dcore, nel, s);
@@ -430,8 +546,37 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
                                 cudaMemcpyHostToDevice, s));
         HTLR_CK(cudaStreamSynchronize(s));  // offs / far_core host buffers go out of scope
     }
+    // inadmissible leaves, generated: per-point diagonal and the near lists only
+    if (H->near_generated) {
+        if (dalloc(H, &H->d_diagpts, (size_t)N) || dalloc(H, &H->d_near_col, H->nnear) ||
+            dalloc(H, &H->d_near_rowptr, H->near_rowptr.size()))
+            return HTLR_ECUDA;
+        if (H->tensor) {
+            std::vector<double> gx, gw;
+            gauss_legendre_host(H->q, gx, gw);
+            double *d_g = nullptr;
+            if (tmp.alloc(&d_g, 2 * (size_t)H->q)) return HTLR_ECUDA;
+            HTLR_CK(cudaMemcpyAsync(d_g, gx.data(), sizeof(double) * H->q, cudaMemcpyHostToDevice, s));
+            HTLR_CK(cudaMemcpyAsync(d_g + H->q, gw.data(), sizeof(double) * H->q,
+                                    cudaMemcpyHostToDevice, s));
+            launch_diag_points(H->kern, d, n, H->d_coords, H->d_edges, H->q, d_g, d_g + H->q,
+                               H->d_diagpts, s);
+            HTLR_CK(cudaGetLastError());
+        } else {
+            std::vector<double> dv((size_t)N, H->diag);  // the same integral at every point
+            HTLR_CK(cudaMemcpyAsync(H->d_diagpts, dv.data(), sizeof(double) * N,
+                                    cudaMemcpyHostToDevice, s));
+            HTLR_CK(cudaStreamSynchronize(s));
+        }
+        HTLR_CK(cudaMemcpyAsync(H->d_near_col, H->near_col.data(), sizeof(int) * H->nnear,
+                                cudaMemcpyHostToDevice, s));
+        HTLR_CK(cudaMemcpyAsync(H->d_near_rowptr, H->near_rowptr.data(),
+                                sizeof(int) * H->near_rowptr.size(), cudaMemcpyHostToDevice, s));
+        HTLR_CK(cudaStreamSynchronize(s));
+        H->nnear_unique = 0;
+    }
     // dense inadmissible leaves
-    {
+    if (!H->near_generated) {
         std::vector<int> offs, taus;
         if (stored) {
             H->near_blk.resize(H->nnear);
@@ -544,8 +689,8 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
         HTLR_CK(cudaMemcpyAsync(Lv.d_row_task, Lv.row_task_begin.data(),
                                 sizeof(int) * Lv.row_task_begin.size(), cudaMemcpyHostToDevice, s));
     }
-    {
-        H->near_task0 = (int)H->tasks.size();
+    H->near_task0 = (int)H->tasks.size();
+    if (!H->near_generated) {
         make_tasks(L + 1, H->near_rowptr, 1 << (d * L),
                    (size_t)H->near_ld * rows_leaf * prec_bytes(H->near_prec), H->near_ld,
                    H->near_row_task);
@@ -585,7 +730,7 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
     st.n = n;
     st.levels = L;
     st.p = p;
-    st.storage = H->storage;
+    st.storage = H->near_generated ? HTLR_STORE_GENERATED : H->storage;
     st.p_eff_leaf = H->orth ? std::min(p, leaf) : p;
     double paper = 0.0;
     for (int lv = 1; lv <= L; ++lv) {
@@ -671,61 +816,133 @@ int launch_streams(const htlr_handle *H, const KindDesc *d_kinds, const double *
     return 2;
 }
 
-static int enqueue_matvec(const htlr_handle *H, const double *u, double *f, int nrhs,
-                          StageEvents *tev = nullptr)
+// Device view of a level's box geometry and factors.
+LevelGeom level_geom(const htlr_handle *H, int lv)
+{
+    const LevelData &Lv = H->lev[lv];
+    const int nb1 = 1 << lv;
+    LevelGeom g{};
+    for (int l = 0; l < 3; ++l) {
+        const int *base = Lv.d_geo + (size_t)(l < H->d ? l : 0) * 4 * nb1;
+        g.first[l] = base;
+        g.cnt[l] = base + nb1;
+        g.uoff[l] = base + 2 * nb1;
+        g.voff[l] = base + 3 * nb1;
+    }
+    g.Upool = Lv.d_Upool;
+    g.Vpool = Lv.d_Vpool;
+    g.level = lv;
+    g.pe = Lv.pe;
+    g.pd = Lv.pd;
+    g.maxcnt = Lv.maxcnt;
+    return g;
+}
+
+// One RHS chunk of HMultVec (stages: up, stream [+ generated near], reduce, out) with the
+// given scratch: W[lv], Hs[lv] per level, task partials, the kinds table.
+int run_chunk(const htlr_handle *H, const KindDesc *d_kinds, double *part,
+              const std::vector<double *> &W, const std::vector<double *> &Hs, const double *uc,
+              double *fc, int nh, StageEvents *tev, cudaStream_t s)
 {
     const int d = H->d, n = H->n, L = H->L;
     const long long N = (long long)ipow(n, d);
-    cudaStream_t s = H->stream;
     int launches = 0;
-    std::vector<DownLevel> down;
+    auto mark = [&](int k) {
+        if (tev) cudaEventRecord(tev->ev[k], s);
+    };
+    mark(0);
+    for (int lv = 1; lv <= L; ++lv) {
+        if (H->lev[lv].nfar == 0) continue;
+        launch_up(d, n, level_geom(H, lv), uc, nh, N, H->nrc, W[lv], s);
+        ++launches;
+    }
+    mark(1);
+    mark(2);
+    if (!H->tasks.empty()) launches += launch_streams(H, d_kinds, uc, N, nh, part, s);
+    if (H->near_generated) {
+        NearGenArgs g{};
+        g.k = H->kern;
+        g.d = d;
+        g.n = n;
+        g.L = L;
+        g.nrhs = nh;
+        g.leafg = level_geom(H, L);
+        g.coords = H->d_coords;
+        g.width = H->d_width;
+        g.diag = H->d_diagpts;
+        g.a = H->d_a;
+        g.rowptr = H->d_near_rowptr;
+        g.col = H->d_near_col;
+        g.u = uc;
+        g.ldu = N;
+        g.f = fc;
+        g.ldf = N;
+        g.max_rows = H->max_leaf_rows;
+        launch_near_generated(H->near_prec, g, s);
+        ++launches;
+    }
+    mark(3);
+    mark(4);
     for (int lv = 1; lv <= L; ++lv) {
         const LevelData &Lv = H->lev[lv];
         if (Lv.nfar == 0) continue;
-        down.push_back(DownLevel{lv, Lv.nb, Lv.pe, Lv.pd, Lv.d_F, Lv.d_H});
+        launch_reduce_far(Lv.nbox, Lv.pd, Lv.ld, H->nrc, nh, Lv.d_row_task, H->d_tasks, part,
+                          Hs[lv], s);
+        ++launches;
     }
-    for (int c0 = 0; c0 < nrhs; c0 += H->nrc) {
-        const int nh = std::min(H->nrc, nrhs - c0);
-        const double *uc = u + (long long)c0 * N;
-        double *fc = f + (long long)c0 * N;
-        auto mark = [&](int k) {
-            if (tev) cudaEventRecord(tev->ev[k], s);
-        };
-        auto close_stage = [&](int st) {
-            if (!tev) return;
+    mark(5);
+    mark(6);
+    OutArgs oa{};
+    oa.d = d;
+    oa.n = n;
+    oa.L = L;
+    oa.nrc = H->nrc;
+    oa.nrhs = nh;
+    oa.leafg = level_geom(H, L);
+    oa.near_row_task = H->d_near_row_task;
+    oa.tasks = H->d_tasks;
+    oa.part = part;
+    oa.near_ld = H->near_ld;
+    oa.a_add = (H->near_generated || H->storage == HTLR_STORE_STORED) ? nullptr : H->d_a;
+    oa.u = uc;
+    oa.ldu = N;
+    oa.near_in_f = H->near_generated;
+    oa.ndown = 0;
+    for (int lv = 1; lv <= L; ++lv) {
+        if (H->lev[lv].nfar == 0) continue;
+        oa.down[oa.ndown].g = level_geom(H, lv);
+        oa.down[oa.ndown].H = Hs[lv];
+        ++oa.ndown;
+    }
+    oa.f = fc;
+    oa.ldf = N;
+    launch_out(oa, H->max_leaf_rows, s);
+    ++launches;
+    mark(7);
+    if (tev)
+        for (int st = 0; st < HTLR_NUM_STAGES; ++st) {
             cudaEventSynchronize(tev->ev[2 * st + 1]);
             float ms = 0.f;
             cudaEventElapsedTime(&ms, tev->ev[2 * st], tev->ev[2 * st + 1]);
             tev->ms[st] += ms;
-        };
-        mark(0);
-        for (int lv = 1; lv <= L; ++lv) {
-            const LevelData &Lv = H->lev[lv];
-            if (Lv.nfar == 0) continue;
-            launch_up(d, n, lv, Lv.nb, Lv.pe, Lv.d_F, uc, nh, N, H->nrc, Lv.d_W, s);
-            ++launches;
         }
-        mark(1);
-        mark(2);
-        launches += launch_streams(H, H->d_kinds, uc, N, nh, H->d_part, s);
-        
-        mark(3);
-        mark(4);
-        for (int lv = 1; lv <= L; ++lv) {
-            const LevelData &Lv = H->lev[lv];
-            if (Lv.nfar == 0) continue;
-            launch_reduce_far(Lv.nbox, Lv.pd, Lv.ld, H->nrc, nh, Lv.d_row_task, H->d_tasks,
-                              H->d_part, Lv.d_H, s);
-            ++launches;
-        }
-        mark(5);
-        mark(6);
-        launch_out(d, n, H->leaf, L, H->nrc, nh, H->d_near_row_task, H->d_tasks, H->d_part,
-                   H->near_ld, H->storage == HTLR_STORE_STORED ? nullptr : H->d_a, uc, N,
-                   down.data(), (int)down.size(), fc, N, s);
-        ++launches;
-        mark(7);
-        for (int st = 0; st < HTLR_NUM_STAGES; ++st) close_stage(st);
+    return launches;
+}
+
+static int enqueue_matvec(const htlr_handle *H, const double *u, double *f, int nrhs,
+                          StageEvents *tev = nullptr)
+{
+    const long long N = (long long)ipow(H->n, H->d);
+    std::vector<double *> W(H->L + 1, nullptr), Hs(H->L + 1, nullptr);
+    for (int lv = 1; lv <= H->L; ++lv) {
+        W[lv] = H->lev[lv].d_W;
+        Hs[lv] = H->lev[lv].d_H;
+    }
+    int launches = 0;
+    for (int c0 = 0; c0 < nrhs; c0 += H->nrc) {
+        const int nh = std::min(H->nrc, nrhs - c0);
+        launches += run_chunk(H, H->d_kinds, H->d_part, W, Hs, u + (long long)c0 * N,
+                              f + (long long)c0 * N, nh, tev, H->stream);
     }
     const_cast<htlr_handle *>(H)->last_launches = launches;
     cudaError_t e = cudaGetLastError();
@@ -763,9 +980,27 @@ int htlr_construct_ex(htlr_handle **out, const htlr_kernel *k, int d, int n, con
     if (d * L > 30) return fail(HTLR_EINVAL, "too many boxes");
     if (r < 1 || r > kMaxP) return fail(HTLR_EINVAL, "r must be in 1..16");
     if (!std::isfinite(eta)) return fail(HTLR_EINVAL, "eta must be finite");
-    if (grid && grid->type == HTLR_GRID_TENSOR)
-        return fail(HTLR_EUNSUPPORTED, "tensor (non-uniform) grids are not supported yet");
-    if (grid && grid->type != HTLR_GRID_UNIFORM) return fail(HTLR_EINVAL, "unknown grid type");
+    const bool tensor = grid && grid->type == HTLR_GRID_TENSOR;
+    if (grid && !tensor && grid->type != HTLR_GRID_UNIFORM)
+        return fail(HTLR_EINVAL, "unknown grid type");
+    if (tensor) {
+        if (!grid->coords || !grid->edges)
+            return fail(HTLR_EINVAL, "a tensor grid needs coords and edges");
+        for (int l = 0; l < d; ++l) {
+            const double *x = grid->coords + (size_t)l * n, *e = grid->edges + (size_t)l * (n + 1);
+            if (e[0] != 0.0 || e[n] != 1.0)
+                return fail(HTLR_EINVAL, "tensor grid: the cell edges must start at 0 and end at 1");
+            for (int i = 0; i < n; ++i) {
+                if (!(e[i] < e[i + 1]) || !(x[i] >= e[i] && x[i] <= e[i + 1]) ||
+                    !std::isfinite(x[i]))
+                    return fail(HTLR_EINVAL, "tensor grid: edges must increase and each "
+                                             "coordinate must lie in its cell");
+            }
+        }
+        if (o && o->orth == 1)
+            return fail(HTLR_EUNSUPPORTED, "tensor grids use the interpolation factors "
+                                           "without orthogonalisation (orth must be 0 or -1)");
+    }
     int q = (o && o->quad_order > 0) ? o->quad_order : 16;
     if (q > 64) return fail(HTLR_EINVAL, "quad_order must be in 1..64");
     if (o && (o->orth < -1 || o->orth > 1)) return fail(HTLR_EINVAL, "orth must be -1, 0 or 1");
@@ -790,7 +1025,8 @@ int htlr_construct_ex(htlr_handle **out, const htlr_kernel *k, int d, int n, con
     H->L = L;
     H->eta = eta;
     H->q = q;
-    H->orth = (o && o->orth == 0) ? 0 : 1;
+    H->tensor = tensor ? 1 : 0;
+    H->orth = (tensor || (o && o->orth == 0)) ? 0 : 1;
     H->far_prec = o ? o->far_precision : kPrecFP64;
     H->near_prec = o ? o->near_precision : kPrecFP64;
     int rc;

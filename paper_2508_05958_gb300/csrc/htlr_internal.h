@@ -74,8 +74,13 @@ struct LevelData {
     int64_t nfar = 0;
     std::vector<int> far_rowptr, far_col, far_core;
     int *d_far_rowptr = nullptr, *d_far_col = nullptr, *d_far_core = nullptr;
-    double *d_F = nullptr;      // nb x pe
+    double *d_F = nullptr;      // uniform grid: nb x pe, the factor of every box
     double *d_R = nullptr;      // pe x p
+    // box geometry along each dimension (1-D box k of this level), see LevelGeom
+    std::vector<int> first[3], cnt[3], uoff[3], voff[3];
+    int *d_geo = nullptr;       // device copy: first, cnt, uoff, voff for each dimension
+    double *d_Upool = nullptr, *d_Vpool = nullptr;
+    int maxcnt = 0;
     void *d_cores = nullptr;    // ncores x (ld * pd) elements of the far precision
     int64_t ncores = 0;
     double *d_W = nullptr, *d_H = nullptr;  // nbox x nrc x pd
@@ -100,6 +105,11 @@ struct htlr_handle {
     double h = 0.0, wgt = 0.0;  // grid step and quadrature weight h^d
     double diag = 0.0;          // K_ii h^d (uniform grid)
     double *d_a = nullptr;      // a(x) natural order or null
+    int tensor = 0;             // 1: tensor (non-uniform) grid given by coordinates / edges
+    int near_generated = 0;     // 1: inadmissible blocks recomputed in every matvec
+    double *d_coords = nullptr, *d_width = nullptr, *d_edges = nullptr;  // d x n (n+1)
+    double *d_diagpts = nullptr;  // per-point K_ii w_i (generated near field)
+    int max_leaf_rows = 0;
     std::vector<htlr::LevelData> lev;  // levels 0..L
     // inadmissible leaves
     int64_t nnear = 0, nnear_unique = 0;
@@ -166,8 +176,6 @@ void launch_near(const KernelDesc &k, int d, int n, int leaf, int ld, double h, 
                  const int *d_tau, double *d_blocks, cudaStream_t s);
 
 // ---- apply.cu -------------------------------------------------------------------
-void launch_up(int d, int n, int level, int nb, int pe, const double *d_F, const double *u,
-               int nrhs_here, long long ldu, int nrc, double *d_W, cudaStream_t s);
 // Arguments of one launch of the block stream over tasks [t0, t1), all of one precision.
 // streaming = true marks the blocks as read once per matvec (evict-first loads).
 struct StreamArgs {
@@ -192,14 +200,74 @@ void launch_stream(int prec, const StreamArgs &a);
 int leaf_level(int n, int leaf);
 void launch_reduce_far(int nbox, int pd, int ld, int nrc, int nrhs_here, const int *d_row_task,
                        const Task *d_tasks, const double *d_part, double *d_H, cudaStream_t s);
+// Geometry of the boxes of one level along each dimension (device arrays indexed by the
+// 1-D box index k < 2^level): grid lines [first, first + cnt) of the box, and where its
+// target factor U (cnt x pe) and source factor V (cnt x pe), column-major, start in the
+// factor pools.  On a uniform grid every box of a level points at the same factor.
+struct LevelGeom {
+    const int *first[3];
+    const int *cnt[3];
+    const int *uoff[3];
+    const int *voff[3];
+    const double *Upool;
+    const double *Vpool;
+    int level, pe, pd, maxcnt;
+};
 struct DownLevel {
-    int level, nb, pe, pd;
-    const double *F;
+    LevelGeom g;
     const double *H;
 };
-void launch_out(int d, int n, int leaf, int L, int nrc, int nrhs_here, const int *d_near_row_task,
-                const Task *d_tasks, const double *d_part, int near_ld, const double *d_a_add,
-                const double *u, long long ldu, const DownLevel *d_down, int ndown, double *f,
-                long long ldf, cudaStream_t s);
+void launch_up(int d, int n, const LevelGeom &g, const double *u, int nrhs_here, long long ldu,
+               int nrc, double *d_W, cudaStream_t s);
+// out: f_tau = base + sum over far levels of H_anc x_l U_l (rows of the leaf).  The base
+// is the sum of the leaf's dense-block task partials [+ a u] (near_in_f = 0), or the
+// value already in f written by the generated near field (near_in_f = 1).
+struct OutArgs {
+    int d, n, L, nrc, nrhs;
+    LevelGeom leafg;             // geometry of the leaf level (first / cnt only)
+    const int *near_row_task;    // per leaf: task range of its dense blocks
+    const Task *tasks;
+    const double *part;
+    int near_ld;
+    const double *a_add;         // add a(x) u when the dense blocks do not hold it
+    const double *u;
+    long long ldu;
+    int near_in_f;
+    int ndown;
+    DownLevel down[HTLR_MAX_LEVELS];
+    double *f;
+    long long ldf;
+};
+void launch_out(const OutArgs &a, int max_rows, cudaStream_t s);
+// Generated near field: f_tau = sum over the leaf's near list of K(x_i, y_j) w_j u_j (j != i)
+// + (diag_i + a_i) u_i, kernel values recomputed in every call.  prec: kPrecFP64 or
+// kPrecFP32 (coordinates taken relative to the target leaf before rounding).
+struct NearGenArgs {
+    KernelDesc k;
+    int d, n, L, nrhs;
+    LevelGeom leafg;
+    const double *coords;  // d * n
+    const double *width;   // d * n cell widths
+    const double *diag;    // N values: K_ii w_i
+    const double *a;       // N values or null
+    const int *rowptr, *col;
+    const double *u;
+    long long ldu;
+    double *f;
+    long long ldf;
+    int max_rows;
+};
+void launch_near_generated(int prec, const NearGenArgs &a, cudaStream_t s);
+// Tensor grids: factors of every (level, dim, box), U(i, mu) = L_mu(x_i) and
+// V(i, mu) = L_mu(x_i) w_i on the Chebyshev points of the box's geometric cell.
+// geo: the level's device geometry array, per dimension [first | cnt | uoff | voff], each
+// 2^level ints.
+void launch_factor_tensor(int d, int n, int level, int p, const double *coords,
+                          const double *width, const int *geo, double *Upool, double *Vpool,
+                          cudaStream_t s);
+// Tensor grids: K_ii w_i = int over the cell of point i of k(x_i, y) dy for every point.
+void launch_diag_points(const KernelDesc &k, int d, int n, const double *coords,
+                        const double *edges, int q, const double *gx, const double *gw,
+                        double *diag, cudaStream_t s);
 
 }  // namespace htlr

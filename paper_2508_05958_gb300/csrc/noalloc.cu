@@ -57,8 +57,10 @@ size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 }  // namespace
 
 bool handle_is_live(const htlr_handle *H);
-int launch_streams(const htlr_handle *H, const KindDesc *d_kinds, const double *u, long long ldu,
-                   int nh, double *part, cudaStream_t s);
+struct StageEvents;
+int run_chunk(const htlr_handle *H, const KindDesc *d_kinds, double *part,
+              const std::vector<double *> &W, const std::vector<double *> &Hs, const double *uc,
+              double *fc, int nh, StageEvents *tev, cudaStream_t s);
 
 int matvec_noalloc(const htlr_handle *H, const double *u, double *f, int nrhs)
 {
@@ -115,33 +117,16 @@ int matvec_noalloc(const htlr_handle *H, const double *u, double *f, int nrhs)
         for (int k = 0; k < d; ++k) v *= n;
         return v;
     }();
-    std::vector<DownLevel> down;
+    std::vector<double *> W(L + 1, nullptr), Hs(L + 1, nullptr);
     for (int lv = 1; lv <= L; ++lv) {
-        const LevelData &Lv = H->lev[lv];
-        if (Lv.nfar == 0) continue;
-        down.push_back(DownLevel{lv, Lv.nb, Lv.pe, Lv.pd, Lv.d_F,
-                                 reinterpret_cast<const double *>(base + h_off[lv])});
+        if (H->lev[lv].nfar == 0) continue;
+        W[lv] = reinterpret_cast<double *>(base + w_off[lv]);
+        Hs[lv] = reinterpret_cast<double *>(base + h_off[lv]);
     }
     for (int c0 = 0; c0 < nrhs; c0 += H->nrc) {
         const int nh = nrhs - c0 < H->nrc ? nrhs - c0 : H->nrc;
-        const double *uc = u + (long long)c0 * N;
-        double *fc = f + (long long)c0 * N;
-        for (int lv = 1; lv <= L; ++lv) {
-            const LevelData &Lv = H->lev[lv];
-            if (Lv.nfar == 0) continue;
-            launch_up(d, n, lv, Lv.nb, Lv.pe, Lv.d_F, uc, nh, N, H->nrc,
-                      reinterpret_cast<double *>(base + w_off[lv]), s);
-        }
-        launch_streams(H, d_kinds, uc, N, nh, part, s);
-        for (int lv = 1; lv <= L; ++lv) {
-            const LevelData &Lv = H->lev[lv];
-            if (Lv.nfar == 0) continue;
-            launch_reduce_far(Lv.nbox, Lv.pd, Lv.ld, H->nrc, nh, Lv.d_row_task, H->d_tasks, part,
-                              reinterpret_cast<double *>(base + h_off[lv]), s);
-        }
-        launch_out(d, n, H->leaf, L, H->nrc, nh, H->d_near_row_task, H->d_tasks, part,
-                   H->near_ld, H->storage == HTLR_STORE_STORED ? nullptr : H->d_a, uc, N,
-                   down.data(), (int)down.size(), fc, N, s);
+        run_chunk(H, d_kinds, part, W, Hs, u + (long long)c0 * N, f + (long long)c0 * N, nh,
+                  nullptr, s);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "htlr_matvec_noalloc launch");

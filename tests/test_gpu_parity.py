@@ -161,6 +161,7 @@ def test_memory_limit_refusal():
 # far field meets the mixed-precision tolerance (1e-6 relative, stated for that mode).
 # ----------------------------------------------------------------------------------
 MIXED_TOL = 1e-6
+FP32_TOL = 1e-5     # far and near fields both in FP32
 
 
 @pytest.mark.parametrize("storage", [1, 2])
@@ -196,3 +197,89 @@ def test_df64_polynomial_exactness_and_determinism(oracle):
     assert np.array_equal(outs[0], outs[1])
     fd = oracle.dense_rows(w.d, w.n, 4, u, param=2, a=w.a())
     assert rel(outs[0], fd) < 1e-12
+
+
+# ----------------------------------------------------------------------------------
+# Tensor (quasi-uniform) grids and the generated near field
+# ----------------------------------------------------------------------------------
+def _qgrid(d, n, seed=5):
+    from paper_2508_05958_gb300.workloads import quasi_uniform_tensor_grid
+    return quasi_uniform_tensor_grid(d, n, seed)
+
+
+def _gpu_tensor(w, grid, u, a=None, **kw):
+    import torch
+    from paper_2508_05958_gb300 import htlr
+    H = htlr.htlr_construct(w.ktype, w.d, w.n, w.leaf, w.p, w.eta, kscale=w.kscale,
+                            kparam=w.kparam, a=a, grid=grid, **kw)
+    try:
+        info = htlr.htlr_info(H)
+        nr = u.shape[1]
+        ud = torch.from_numpy(np.ascontiguousarray(u.T)).cuda()
+        fd = torch.full_like(ud, float("nan"))
+        htlr.htlr_matvec(H, ud, fd, nr)
+        htlr.htlr_sync(H)
+        return fd.cpu().numpy().T.copy(), info
+    finally:
+        htlr.htlr_free(H)
+
+
+@pytest.mark.parametrize("d,n,leaf,p,eta", [(2, 32, 4, 4, 1.0), (3, 16, 4, 3, 1.0),
+                                            (3, 16, 2, 3, 0.0)])
+def test_tensor_grid_polynomial_exact(oracle, d, n, leaf, p, eta):
+    from paper_2508_05958_gb300.workloads import Workload
+    w = Workload("tp", d=d, n=n, ktype=4, leaf=leaf, p=p, eta=eta, kparam=p - 1, seed=31)
+    grid = _qgrid(d, n)
+    u = w.u(nrhs=2)
+    a = np.random.default_rng(3).uniform(0.5, 1.5, w.N)
+    f, info = _gpu_tensor(w, grid, u, a=a)
+    assert info["storage"] == 3
+    fd = oracle.dense_rows(d, n, 4, u, param=p - 1, a=a, grid=grid)
+    assert rel(f, fd) < 1e-12
+
+
+@pytest.mark.parametrize("ktype", [2, 1])
+def test_tensor_grid_matches_oracle_htlr(oracle, ktype):
+    from paper_2508_05958_gb300.workloads import Workload
+    w = Workload("tq", d=3, n=32, ktype=ktype, leaf=4, p=4, eta=1.0, seed=32)
+    grid = _qgrid(3, 32, seed=7)
+    u = w.u(nrhs=3)
+    f, info = _gpu_tensor(w, grid, u)
+    H = oracle.HTLR(3, 32, ktype, 4, 4, 1.0, grid=grid, orth=False)
+    ref = H.matvec(u)
+    assert info["far_per_level"] == H.stats()[0]
+    assert rel(f, ref) < TOL
+    # mixed precision (FP32 far field, FP64 near field) stays within the mixed tolerance;
+    # with the generated near field in FP32 too, within the looser FP32 bound
+    fmix, _ = _gpu_tensor(w, grid, u, far_precision=2, near_precision=0)
+    assert rel(fmix, ref) < MIXED_TOL
+    f32, _ = _gpu_tensor(w, grid, u, far_precision=2, near_precision=2)
+    assert rel(f32, ref) < FP32_TOL
+
+
+@pytest.mark.parametrize("near", [0, 2])
+def test_uniform_generated_near_field(oracle, near):
+    from paper_2508_05958_gb300.workloads import workload
+    w = workload("c2", n=16)
+    u = w.u(nrhs=5)
+    f, info = gpu_matvec(w, u, storage=3, near_precision=near)
+    assert info["storage"] == 3 and info["unique_near"] == 0
+    ref, _ = _oracle_htlr(oracle, w, u)
+    assert rel(f, ref) < (TOL if near == 0 else FP32_TOL)
+
+
+def test_tensor_grid_rejects_empty_boxes_and_orth():
+    from paper_2508_05958_gb300 import htlr
+    x = np.tile((np.arange(8) + 0.5) / 8, (2, 1))
+    x[0] = np.linspace(0.01, 0.3, 8)              # nothing in the upper half of dim 1
+    e = np.zeros((2, 9))
+    for l in range(2):
+        e[l, 1:8] = 0.5 * (x[l, :-1] + x[l, 1:])
+        e[l, 8] = 1.0
+    with pytest.raises(htlr.HTLRError) as ei:
+        htlr.htlr_construct(2, 2, 8, 2, 3, 1.0, grid=(x, e))
+    assert ei.value.code == htlr.HTLR_EINVAL
+    g = _qgrid(2, 16)
+    with pytest.raises(htlr.HTLRError) as ei:
+        htlr.htlr_construct(2, 2, 16, 4, 3, 1.0, grid=g, orth=1)
+    assert ei.value.code == htlr.HTLR_EUNSUPPORTED
