@@ -203,6 +203,40 @@ int htlr_matvec_timed(const htlr_handle *H, const double *u, double *f, int nrhs
  */
 int htlr_matvec_noalloc(const htlr_handle *H, const double *u, double *f, int nrhs);
 
+/* Options of htlr_gmres (NULL: restart 30, max_iters 3000, tol 1e-10, inner_tol 1e-6,
+ * max_refine 20). */
+typedef struct {
+    int restart;       /* Krylov dimension m of GMRES(m), 1..200 */
+    int max_iters;     /* total Arnoldi steps over all restarts (and refinements) */
+    double tol;        /* target ||f - A u|| / ||f|| per right-hand side (A: the operator H) */
+    double inner_tol;  /* refinement only: relative tolerance of each inner solve */
+    int max_refine;    /* refinement only: maximum correction steps */
+} htlr_gmres_options;
+
+typedef struct {
+    int iterations;      /* Arnoldi steps taken (all restarts and refinements) */
+    int matvecs;         /* operator applications (each one covers all nrhs) */
+    int refinements;     /* correction steps (0 without an inner operator) */
+    double rel_residual; /* max over the right-hand sides of ||f - A u|| / ||f||, A = H */
+    int converged;       /* 1 if rel_residual <= tol */
+} htlr_gmres_result;
+
+/*
+ * htlr_gmres -- solve a(x) u + K u = f (the inversion of eq. (1.1); A applied by
+ * HMultVec) for nrhs right-hand sides with restarted GMRES(m): FP64 Arnoldi with
+ * classical Gram-Schmidt applied twice, Givens rotations, true residual at each restart.
+ *   H        the operator whose residual defines convergence (FP64 or df64 for 1e-10).
+ *   H_inner  NULL, or an operator of the same grid (typically mixed precision): then the
+ *            solve is iterative refinement -- r = f - H u, H_inner e = r solved to
+ *            inner_tol, u += e -- until ||r|| <= tol ||f||.
+ *   f, u     device pointers, N x nrhs column-major; u holds the initial guess and
+ *            receives the solution.
+ * Allocates its Krylov workspace ((restart + 4) N nrhs doubles) for the call.
+ * Synchronous.  Errors as htlr_matvec; HTLR_EINVAL for bad options.
+ */
+int htlr_gmres(const htlr_handle *H, const htlr_handle *H_inner, const double *f, double *u,
+               int nrhs, const htlr_gmres_options *o, htlr_gmres_result *res);
+
 /* Release everything the handle owns.  NULL is a no-op.  A second free of the same
  * handle is detected through a magic word and ignored (reported by htlr_last_error). */
 void htlr_free(htlr_handle *H);

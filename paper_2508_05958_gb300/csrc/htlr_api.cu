@@ -930,7 +930,16 @@ int run_chunk(const htlr_handle *H, const KindDesc *d_kinds, double *part,
 }
 
 static int enqueue_matvec(const htlr_handle *H, const double *u, double *f, int nrhs,
-                          StageEvents *tev = nullptr)
+                          StageEvents *tev = nullptr);
+
+// HMultVec for other parts of the library (GMRES): enqueue on the handle's stream.
+int matvec_enqueue(const htlr_handle *H, const double *u, double *f, int nrhs)
+{
+    return enqueue_matvec(H, u, f, nrhs);
+}
+
+static int enqueue_matvec(const htlr_handle *H, const double *u, double *f, int nrhs,
+                          StageEvents *tev)
 {
     const long long N = (long long)ipow(H->n, H->d);
     std::vector<double *> W(H->L + 1, nullptr), Hs(H->L + 1, nullptr);

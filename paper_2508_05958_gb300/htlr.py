@@ -23,7 +23,7 @@ MAX_LEVELS = 16
 
 NUM_STAGES = 4
 SYMBOLS = ("htlr_construct", "htlr_construct_ex", "htlr_matvec", "htlr_matvec_timed",
-           "htlr_matvec_host", "htlr_matvec_noalloc", "htlr_free",
+           "htlr_matvec_host", "htlr_matvec_noalloc", "htlr_gmres", "htlr_free",
            "htlr_info", "htlr_set_stream", "htlr_sync", "htlr_last_error",
            "htlr_last_launch_count")
 
@@ -59,6 +59,17 @@ class htlr_stats(ctypes.Structure):
                 ("bytes_work", ctypes.c_size_t), ("bytes_total", ctypes.c_size_t),
                 ("diag_value", ctypes.c_double), ("far_precision", ctypes.c_int),
                 ("near_precision", ctypes.c_int)]
+
+
+class htlr_gmres_options(ctypes.Structure):
+    _fields_ = [("restart", ctypes.c_int), ("max_iters", ctypes.c_int), ("tol", ctypes.c_double),
+                ("inner_tol", ctypes.c_double), ("max_refine", ctypes.c_int)]
+
+
+class htlr_gmres_result(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("matvecs", ctypes.c_int),
+                ("refinements", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("converged", ctypes.c_int)]
 
 
 _lock = threading.Lock()
@@ -97,6 +108,9 @@ def load(build_if_missing: bool = True):
         L.htlr_matvec.restype = ctypes.c_int
         L.htlr_matvec_timed.argtypes = [vp, vp, vp, ctypes.c_int, P(ctypes.c_float)]
         L.htlr_matvec_timed.restype = ctypes.c_int
+        L.htlr_gmres.argtypes = [vp, vp, vp, vp, ctypes.c_int, P(htlr_gmres_options),
+                                 P(htlr_gmres_result)]
+        L.htlr_gmres.restype = ctypes.c_int
         L.htlr_matvec_noalloc.argtypes = [vp, vp, vp, ctypes.c_int]
         L.htlr_matvec_noalloc.restype = ctypes.c_int
         L.htlr_matvec_host.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_double), ctypes.c_int]
@@ -182,6 +196,20 @@ def htlr_matvec(H, u, f, nrhs=None):
     if nrhs is None:
         nrhs = 1 if u.dim() == 1 else u.shape[0]
     _check(load().htlr_matvec(H, _dptr(u), _dptr(f), nrhs))
+
+
+def htlr_gmres(H, f, u, nrhs=None, H_inner=None, restart=30, max_iters=3000, tol=1e-10,
+               inner_tol=1e-6, max_refine=20) -> dict:
+    """Solve A u = f (A = a I + K applied by H) with restarted GMRES; with H_inner, by
+    iterative refinement around inner solves with H_inner.  u: initial guess, overwritten.
+    Returns the result counters as a dict."""
+    if nrhs is None:
+        nrhs = 1 if f.dim() == 1 else f.shape[0]
+    o = htlr_gmres_options(restart, max_iters, tol, inner_tol, max_refine)
+    r = htlr_gmres_result()
+    _check(load().htlr_gmres(H, H_inner, _dptr(f), _dptr(u), nrhs, ctypes.byref(o),
+                             ctypes.byref(r)))
+    return {name: getattr(r, name) for name, _ in htlr_gmres_result._fields_}
 
 
 def htlr_matvec_noalloc(H, u, f, nrhs=None):
