@@ -40,9 +40,11 @@ def parse():
     ap.add_argument("--impl", default="htlr", choices=["htlr", "reference"])
     ap.add_argument("--config", default="c2")
     ap.add_argument("--storage", type=int, default=1, help="1 STORED, 2 SHARED, 0 AUTO")
-    ap.add_argument("--far-precision", type=int, default=1, help="0 FP64, 1 DF64, 2 FP32")
-    ap.add_argument("--near-precision", type=int, default=1, help="0 FP64, 1 DF64, 2 FP32")
+    ap.add_argument("--far-precision", type=int, default=1, help="0 FP64, 1 DF64, 2 FP32, 3 BF16X6 (tensor cores)")
+    ap.add_argument("--near-precision", type=int, default=1, help="0 FP64, 1 DF64, 2 FP32, 3 BF16X6 (tensor cores)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--gmres-solves", type=int, default=20,
+                    help="GMRES solves (to 1e-10) timed after the matvec, per variant")
     ap.add_argument("--cpu-sample-s", type=float, default=20.0)
     return ap.parse_args()
 
@@ -203,8 +205,8 @@ def run_reference(args, w):
 # ----------------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------------
-PREC_NAME = {0: "f64", 1: "df64", 2: "f32"}
-PREC_BYTES = {0: 8, 1: 8, 2: 4}
+PREC_NAME = {0: "f64", 1: "df64", 2: "f32", 3: "bf16x6"}
+PREC_BYTES = {0: 8, 1: 8, 2: 4, 3: 6}
 # multiply-adds per second of the stream's inner loop, from unit counts and clocks
 # (152 SMs at 2.07 GHz): FP64 2 FMA/clk/SM (the nominal 1.25 TFLOP/s); FP32 128 lanes;
 # df64 spends 12 FP32-pipe instructions per multiply-add (see stream_impl.cuh)
@@ -233,8 +235,49 @@ def stream_elements(info, w):
     return far, near, far_unique, near_unique
 
 
-def stream_roofline(info, w, nrhs, stream_ms, hbm_peak, hbm_src):
+def tc_tensor_flops(info, w, nrhs):
+    """BF16 tensor-core FLOPs the BF16X6 stream executes for one RHS chunk: six MMAs per
+    multiply-add on padded tiles (128-row M-tiles, K padded to the chunk, N = RHS rounded
+    up to 16)."""
+    def shape(rows):
+        mt = (rows + 127) // 128
+        kc = 16
+        for k in (64, 32, 16):
+            stage = 3 * mt * 128 * k * 2 + 3 * 64 * k * 2
+            kc = k
+            if stage * 3 <= 210 * 1024:
+                break
+        return mt * 128, -(-rows // kc) * kc
+    rp = -(-min(nrhs, 64) // 16) * 16
+    total = 0.0
+    for lv, nfar in enumerate(info["far_per_level"]):
+        if nfar:
+            pd = min(w.p, w.n >> lv) ** w.d
+            m, k = shape(pd)
+            total += nfar * 12.0 * m * k * rp
+    if info["near_precision"] == 3:
+        m, k = shape(w.leaf ** w.d)
+        total += info["near_blocks"] * 12.0 * m * k * rp
+    return total * -(-nrhs // 64)
+
+
+def stream_roofline(info, w, nrhs, stream_ms, hbm_peak, hbm_src, bf16_peak=None):
     fp, np_ = info["far_precision"], info["near_precision"]
+    if fp == 3:
+        far, near, far_u, near_u = stream_elements(info, w)
+        t = stream_ms * 1e-3
+        executed = tc_tensor_flops(info, w, nrhs)
+        peak = bf16_peak or 1895.3
+        useful = 2.0 * (far + (near if np_ == 3 else 0.0)) * nrhs
+        held = far_u * PREC_BYTES[fp] + (near_u * PREC_BYTES[np_] if info["storage"] != 3 else 0)
+        return {"bound": "tensor", "achieved": executed / t / 1e12, "peak": peak,
+                "algorithmic_bytes_per_launch": held, "hbm_achieved_gbs": held / t / 1e9,
+                "unit": "TFLOP/s", "frac": executed / t / 1e12 / peak,
+                "peak_source": "measured bf16 (MEASURED_PEAKS.json, burst)",
+                "kernel": "tc_stream_kernel (tcgen05 kind::f16, BF16x6)", "kernel_ms": stream_ms,
+                "executed_tensor_flops_per_launch": executed,
+                "useful_fp32_equivalent_tflops": useful / t / 1e12, "traffic": None,
+                "precision": {"far": PREC_NAME[fp], "near": PREC_NAME[np_]}}
     far, near, far_u, near_u = stream_elements(info, w)
     t = stream_ms * 1e-3
     hbm_bytes = far_u * PREC_BYTES[fp] + near_u * PREC_BYTES[np_]
@@ -259,6 +302,48 @@ def stream_roofline(info, w, nrhs, stream_ms, hbm_peak, hbm_src):
                 "frac": ach / hbm_peak, "peak_source": hbm_src}
     roof.update(base)
     return roof
+
+
+def time_gmres(w, solves, stream):
+    """Solve latency of a(x)u + Ku = f to 1e-10 (GMRES(30) from u = 0, seeded f ~ N(0,1)):
+    plain FP64 operator versus df64 residual operator with an FP32 far field inner
+    operator (iterative refinement).  Each solve is timed with CUDA events."""
+    import torch
+    from paper_2508_05958_gb300 import htlr
+    out = {}
+    variants = {"fp64": ((0, 0), None), "mixed_refined": ((1, 1), (2, 1))}
+    for name, (acc, inner) in variants.items():
+        H = htlr.htlr_construct(w.ktype, w.d, w.n, w.leaf, w.p, w.eta, kscale=w.kscale,
+                                kparam=w.kparam, a=w.a(), far_precision=acc[0],
+                                near_precision=acc[1], stream=stream)
+        Hi = None
+        if inner:
+            Hi = htlr.htlr_construct(w.ktype, w.d, w.n, w.leaf, w.p, w.eta, kscale=w.kscale,
+                                     kparam=w.kparam, a=w.a(), far_precision=inner[0],
+                                     near_precision=inner[1], stream=stream)
+        f = torch.from_numpy(np.ascontiguousarray(w.u(nrhs=1, seed=500).T)).cuda()
+        u = torch.zeros_like(f)
+        htlr.htlr_gmres(H, f, u, 1, H_inner=Hi)          # warm-up
+        times, res = [], None
+        for k in range(solves):
+            f = torch.from_numpy(np.ascontiguousarray(w.u(nrhs=1, seed=501 + k).T)).cuda()
+            u.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = htlr.htlr_gmres(H, f, u, 1, H_inner=Hi)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        htlr.htlr_free(H)
+        if Hi:
+            htlr.htlr_free(Hi)
+        times.sort()
+        out[name] = {"p50_ms": times[len(times) // 2],
+                     "p99_ms": times[min(len(times) - 1, int(0.99 * len(times)))],
+                     "solves_per_s": 1e3 / float(np.mean(times)), "iterations": res["iterations"],
+                     "refinements": res["refinements"], "rel_residual": res["rel_residual"]}
+    return out
 
 
 def run_gpu(args, w):
@@ -335,7 +420,8 @@ def run_gpu(args, w):
     stage_ms = stage / args.steps
 
     # roofline of the dominant kernel (the block stream)
-    roof = stream_roofline(info, w, nrhs, stage_ms[1], hbm_peak, hbm_src)
+    roof = stream_roofline(info, w, nrhs, stage_ms[1], hbm_peak, hbm_src,
+                           peaks.get("bf16_tflops"))
 
     # end to end through the host-buffer entry point (pinned host memory, copies timed)
     uh = torch.from_numpy(np.ascontiguousarray(U.T)).pin_memory().numpy()
@@ -367,6 +453,8 @@ def run_gpu(args, w):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
     }
+    if args.gmres_solves > 0 and w.a_kind != "zero":
+        line["gmres"] = time_gmres(w, args.gmres_solves, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         val, cores, sample, _ = time_oracle(w, args.cpu_sample_s)
         line["cpu_baseline"] = {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",

@@ -95,7 +95,12 @@ typedef enum {
                             products formed with error-free FP32 transformations; results
                             within ~1e-14 of FP64.  Entries must lie within FP32 range,
                             |x| in [1e-30, 1e30], for that accuracy */
-    HTLR_PREC_FP32 = 2   /* FP32 blocks, products and accumulation (~1e-7 relative) */
+    HTLR_PREC_FP32 = 2,  /* FP32 blocks, products and accumulation (~1e-7 relative) */
+    HTLR_PREC_BF16X6 = 3 /* tensor cores (tcgen05): operands split into three BF16 terms,
+                            the six products a_i b_j with i + j <= 4 accumulated in FP32
+                            (FP32-class accuracy); the many-right-hand-side path.  The far
+                            field in BF16X6 needs a BF16X6 or generated near field;
+                            right-hand sides are processed 64 at a time */
 } htlr_precision;
 
 typedef struct {

@@ -204,6 +204,7 @@ __global__ void __launch_bounds__(256) out_kernel(OutArgs A)
                 for (int k = A.near_row_task[tau]; k < A.near_row_task[tau + 1]; ++k)
                     s += A.part[A.tasks[k].part + (long long)r * A.near_ld + i];
                 if (A.a_add) s += A.a_add[na] * A.u[na + A.ldu * r];
+                if (A.diag_add) s += A.diag_add[na] * A.u[na + A.ldu * r];
             }
             acc[m] = s;
         }

@@ -353,6 +353,25 @@ void launch_near(const KernelDesc &k, int d, int n, int leaf, int ld, double h, 
 }
 
 // ---------------------------------------------------------------------------------
+// Remove the diagonal entries of the listed dense blocks (they are added separately, in
+// FP64, when the blocks are used in a lower precision).
+// ---------------------------------------------------------------------------------
+__global__ void zero_diag_kernel(double *blocks, int ld, int rows, const int *ids, int nids)
+{
+    const long long total = (long long)nids * rows;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int b = ids[idx / rows], i = (int)(idx % rows);
+        blocks[(long long)b * ld * rows + (long long)i * ld + i] = 0.0;
+    }
+}
+
+void launch_zero_diag(double *blocks, int ld, int rows, const int *d_ids, int nids, cudaStream_t s)
+{
+    if (nids > 0) zero_diag_kernel<<<152 * 4, 256, 0, s>>>(blocks, ld, rows, d_ids, nids);
+}
+
+// ---------------------------------------------------------------------------------
 // Tensor grids (§3.3 weights, Def. 3.3 tensor boxes): factors of every 1-D box of a
 // level.  U(i, mu) = L_mu(x_i) and V(i, mu) = L_mu(x_i) w_i on the Chebyshev points of
 // the box's geometric cell [k 2^-l, (k+1) 2^-l], barycentric form; w_i is the 1-D cell

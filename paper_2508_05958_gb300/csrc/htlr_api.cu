@@ -130,6 +130,33 @@ struct Sizes {
     size_t total() const { return cores + near + factors + work + lists; }
 };
 
+// Packed split-BF16 shape of rows x cols blocks: 128-row M-tiles; the K chunk is the
+// largest of 64, 32, 16 columns for which three pipeline stages of (A chunk + B chunk for
+// kTcRpMax right-hand sides) fit in 210 KB of shared memory.
+static TcShape tc_shape(int rows, int cols)
+{
+    TcShape t;
+    t.rows = rows;
+    t.cols = cols;
+    t.mtiles = (rows + 127) / 128;
+    for (int kc : {64, 32, 16}) {  // BF16 MMAs take K in steps of 16
+        t.kc = kc;
+        if (tc_stage_bytes(t.mtiles, kc, kTcRpMax) * 3 <= 210 * 1024) break;
+    }
+    t.nchunks = (cols + t.kc - 1) / t.kc;
+    t.blk_elems = (long long)t.nchunks * 3 * t.mtiles * 128 * t.kc;
+    t.x_elems = (long long)t.nchunks * 3 * kTcRpMax * t.kc;
+    return t;
+}
+
+// Pipeline depth for a shape and a right-hand-side count (at most 210 KB of stages).
+static int tc_stages(const TcShape &t, int Rp)
+{
+    int S = (int)((210 * 1024) / tc_stage_bytes(t.mtiles, t.kc, Rp));
+    if (S > kTcMaxStages) S = kTcMaxStages;
+    return S < 2 ? 2 : S;
+}
+
 static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
 {
     const int d = H->d, n = H->n, leaf = H->leaf, p = H->p, L = H->L;
@@ -294,7 +321,18 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
         Lv.ld = round_up(Lv.pd, 32);
         if (Lv.ld / 32 > 16)
             return fail(HTLR_EUNSUPPORTED, "p_eff^d above 512 is not supported");
+        Lv.tc = tc_shape(Lv.pd, Lv.pd);
     }
+    H->near_tc = tc_shape(rows_leaf, rows_leaf);
+    // tensor-core stream: both block lists on the tensor cores, or far field on the
+    // tensor cores with a generated near field
+    if (H->near_prec == kPrecBF16X6 && (H->far_prec != kPrecBF16X6 || H->near_generated))
+        return fail(HTLR_EUNSUPPORTED, "a BF16X6 near field needs stored dense blocks and a "
+                                       "BF16X6 far field");
+    if (H->far_prec == kPrecBF16X6 && H->near_prec != kPrecBF16X6 && !H->near_generated)
+        return fail(HTLR_EUNSUPPORTED, "a BF16X6 far field needs a BF16X6 or generated near "
+                                       "field");
+    H->tc = (H->far_prec == kPrecBF16X6) ? 1 : 0;
 
     // unique offsets (tau - sigma) per level and for the inadmissible leaves
     auto offset_key = [&](int tau, int sig, int level) {
@@ -348,7 +386,7 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
 
     // tasks: runs of consecutive entries of one row, about kTaskBytes of blocks each
     const size_t kTaskBytes = 256 * 1024;
-    H->nrc = 4;
+    H->nrc = H->tc ? kTcRpMax : 4;
     auto count_tasks = [&](const std::vector<int> &rowptr, int nrows, size_t blk_bytes) {
         long long per = std::max<long long>(1, (long long)(kTaskBytes / blk_bytes));
         long long nt = 0;
@@ -363,8 +401,10 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
     for (int lv = 1; lv <= L; ++lv) {
         LevelData &Lv = H->lev[lv];
         if (Lv.nfar == 0) continue;
-        size_t blk = (size_t)Lv.ld * Lv.pd * prec_bytes(H->far_prec);
-        auto ct = count_tasks(Lv.far_rowptr, Lv.nbox, blk);
+        size_t blk = H->tc ? (size_t)Lv.tc.blk_elems * 4
+                           : (size_t)Lv.ld * Lv.pd * prec_bytes(H->far_prec);
+        // tensor-core tasks are whole block rows (one per row)
+        auto ct = count_tasks(Lv.far_rowptr, Lv.nbox, H->tc ? 1 : blk);
         ntasks += ct.first;
         part_doubles += ct.first * (long long)H->nrc * Lv.ld;
         sz_stored.cores += blk * Lv.nfar;
@@ -389,8 +429,10 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
             z->work += work;
         }
     } else {
-        size_t blk = (size_t)H->near_ld * rows_leaf * prec_bytes(H->near_prec);
-        auto ct = count_tasks(H->near_rowptr, 1 << (d * L), blk);
+        size_t blk = H->near_prec == kPrecBF16X6
+                         ? (size_t)H->near_tc.blk_elems * 4
+                         : (size_t)H->near_ld * rows_leaf * prec_bytes(H->near_prec);
+        auto ct = count_tasks(H->near_rowptr, 1 << (d * L), H->near_prec == kPrecBF16X6 ? 1 : blk);
         ntasks += ct.first;
         part_doubles += ct.first * (long long)H->nrc * H->near_ld;
         sz_stored.near = blk * H->nnear;
@@ -511,7 +553,7 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
             // float pairs (df64), or converted to FP32
             const size_t nel = (size_t)Lv.ncores * Lv.ld * Lv.pd;
             double *dcore = nullptr;
-            if (H->far_prec == kPrecFP32) {
+            if (H->far_prec == kPrecFP32 || H->far_prec == kPrecBF16X6) {
                 HTLR_CK(cudaMalloc(&dcore, nel * sizeof(double)));
             } else if (dalloc(H, &dcore, nel)) {
                 return HTLR_ECUDA;
@@ -532,6 +574,19 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
                 if (rc2) return rc2;
                 HTLR_CK(e2);
                 Lv.d_cores = f32;
+            }
+            if (H->far_prec == kPrecBF16X6) {
+                // packed split-BF16 chunks for the tensor-core stream
+                uint16_t *pk = nullptr;
+                int rc2 = dalloc(H, &pk, (size_t)Lv.ncores * Lv.tc.blk_elems);
+                if (rc2 == HTLR_OK)
+                    launch_tc_pack_blocks(dcore, Lv.ncores, Lv.ld, Lv.pd, Lv.pd, Lv.tc.mtiles,
+                                          Lv.tc.kc, Lv.tc.nchunks, pk, s);
+                cudaError_t e2 = cudaStreamSynchronize(s);
+                cudaFree(dcore);
+                if (rc2) return rc2;
+                HTLR_CK(e2);
+                Lv.d_cores = pk;
             }
             HTLR_CK(cudaGetLastError());
         }
@@ -613,7 +668,7 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
             return HTLR_ECUDA;
         const size_t nel = (size_t)H->nnear_unique * H->near_ld * rows_leaf;
         double *dnear = nullptr;
-        if (H->near_prec == kPrecFP32) {
+        if (H->near_prec == kPrecFP32 || H->near_prec == kPrecBF16X6) {
             HTLR_CK(cudaMalloc(&dnear, nel * sizeof(double)));
         } else if (dalloc(H, &dnear, nel)) {
             return HTLR_ECUDA;
@@ -633,6 +688,37 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
             if (rc2) return rc2;
             HTLR_CK(e2);
             H->d_near = f32;
+        }
+        if (H->near_prec == kPrecBF16X6) {
+            // the diagonal entries (K_ii w_i, with a_i when folded) stay out of the split
+            // blocks: out_kernel adds them to f in FP64
+            std::vector<int> ids;
+            const int nleaf = 1 << (d * L);
+            for (int t = 0; t < nleaf; ++t)
+                for (int e = H->near_rowptr[t]; e < H->near_rowptr[t + 1]; ++e)
+                    if (H->near_col[e] == t) ids.push_back(H->near_blk[e]);
+            std::sort(ids.begin(), ids.end());
+            ids.erase(std::unique(ids.begin(), ids.end()), ids.end());
+            int *d_ids = nullptr;
+            if (tmp.alloc(&d_ids, ids.size())) return HTLR_ECUDA;
+            HTLR_CK(cudaMemcpyAsync(d_ids, ids.data(), sizeof(int) * ids.size(),
+                                    cudaMemcpyHostToDevice, s));
+            launch_zero_diag(dnear, H->near_ld, rows_leaf, d_ids, (int)ids.size(), s);
+            std::vector<double> dv((size_t)N, H->diag);
+            if (dalloc(H, &H->d_diagpts, (size_t)N)) return HTLR_ECUDA;
+            HTLR_CK(cudaMemcpyAsync(H->d_diagpts, dv.data(), sizeof(double) * N,
+                                    cudaMemcpyHostToDevice, s));
+            HTLR_CK(cudaStreamSynchronize(s));
+            uint16_t *pk = nullptr;
+            int rc2 = dalloc(H, &pk, (size_t)H->nnear_unique * H->near_tc.blk_elems);
+            if (rc2 == HTLR_OK)
+                launch_tc_pack_blocks(dnear, H->nnear_unique, H->near_ld, rows_leaf, rows_leaf,
+                                      H->near_tc.mtiles, H->near_tc.kc, H->near_tc.nchunks, pk, s);
+            cudaError_t e2 = cudaStreamSynchronize(s);
+            cudaFree(dnear);
+            if (rc2) return rc2;
+            HTLR_CK(e2);
+            H->d_near = pk;
         }
         HTLR_CK(cudaGetLastError());
         HTLR_CK(cudaMemcpyAsync(H->d_near_col, H->near_col.data(), sizeof(int) * H->nnear,
@@ -669,8 +755,12 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
     for (int lv = 1; lv <= L; ++lv) {
         LevelData &Lv = H->lev[lv];
         if (Lv.nfar == 0) continue;
-        make_tasks(lv, Lv.far_rowptr, Lv.nbox, (size_t)Lv.ld * Lv.pd * prec_bytes(H->far_prec),
-                   Lv.ld, Lv.row_task_begin);
+        if (H->tc) {
+            Lv.row_task_begin.assign(Lv.nbox + 1, (int)H->tasks.size());  // no CUDA-core tasks
+        } else {
+            make_tasks(lv, Lv.far_rowptr, Lv.nbox, (size_t)Lv.ld * Lv.pd * prec_bytes(H->far_prec),
+                       Lv.ld, Lv.row_task_begin);
+        }
         KindDesc &K = H->kinds[lv];
         K.col = Lv.d_far_col;
         K.blk = Lv.d_far_core;
@@ -691,9 +781,12 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
     }
     H->near_task0 = (int)H->tasks.size();
     if (!H->near_generated) {
-        make_tasks(L + 1, H->near_rowptr, 1 << (d * L),
-                   (size_t)H->near_ld * rows_leaf * prec_bytes(H->near_prec), H->near_ld,
-                   H->near_row_task);
+        if (H->near_prec == kPrecBF16X6)
+            H->near_row_task.assign((1 << (d * L)) + 1, (int)H->tasks.size());
+        else
+            make_tasks(L + 1, H->near_rowptr, 1 << (d * L),
+                       (size_t)H->near_ld * rows_leaf * prec_bytes(H->near_prec), H->near_ld,
+                       H->near_row_task);
         KindDesc &K = H->kinds[L + 1];
         K.col = H->d_near_col;
         K.blk = H->d_near_blk;
@@ -711,6 +804,56 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
         if (dalloc(H, &H->d_near_row_task, H->near_row_task.size())) return HTLR_ECUDA;
         HTLR_CK(cudaMemcpyAsync(H->d_near_row_task, H->near_row_task.data(),
                                 sizeof(int) * H->near_row_task.size(), cudaMemcpyHostToDevice, s));
+    }
+    // tensor-core stream: one task per non-empty block row, partials for kTcRpMax RHS
+    if (H->tc) {
+        long long ptc = 0;
+        auto row_tasks = [&](int kind, const std::vector<int> &rowptr, int nrows, int ld,
+                             std::vector<int> &row_task) {
+            row_task.assign(nrows + 1, 0);
+            for (int t = 0; t < nrows; ++t) {
+                row_task[t] = (int)H->tasks_tc.size();
+                if (rowptr[t + 1] > rowptr[t]) {
+                    Task T;
+                    T.kind = kind;
+                    T.row = t;
+                    T.e0 = rowptr[t];
+                    T.e1 = rowptr[t + 1];
+                    T.part = ptc;
+                    ptc += (long long)kTcRpMax * ld;
+                    H->tasks_tc.push_back(T);
+                }
+            }
+            row_task[nrows] = (int)H->tasks_tc.size();
+        };
+        for (int lv = 1; lv <= L; ++lv) {
+            LevelData &Lv = H->lev[lv];
+            if (Lv.nfar == 0) continue;
+            Lv.tc_t0 = (int)H->tasks_tc.size();
+            row_tasks(lv, Lv.far_rowptr, Lv.nbox, Lv.ld, Lv.row_task_tc);
+            Lv.tc_t1 = (int)H->tasks_tc.size();
+            if (dalloc(H, &Lv.d_row_task_tc, Lv.row_task_tc.size()) ||
+                dalloc(H, &Lv.d_Wp, (size_t)Lv.nbox * Lv.tc.x_elems))
+                return HTLR_ECUDA;
+            HTLR_CK(cudaMemcpyAsync(Lv.d_row_task_tc, Lv.row_task_tc.data(),
+                                    sizeof(int) * Lv.row_task_tc.size(), cudaMemcpyHostToDevice, s));
+        }
+        if (H->near_prec == kPrecBF16X6) {
+            H->near_tc_t0 = (int)H->tasks_tc.size();
+            row_tasks(L + 1, H->near_rowptr, 1 << (d * L), H->near_ld, H->near_row_task_tc);
+            H->near_tc_t1 = (int)H->tasks_tc.size();
+            if (dalloc(H, &H->d_near_row_task_tc, H->near_row_task_tc.size()) ||
+                dalloc(H, &H->d_Up, (size_t)(1 << (d * L)) * H->near_tc.x_elems))
+                return HTLR_ECUDA;
+            HTLR_CK(cudaMemcpyAsync(H->d_near_row_task_tc, H->near_row_task_tc.data(),
+                                    sizeof(int) * H->near_row_task_tc.size(),
+                                    cudaMemcpyHostToDevice, s));
+        }
+        if (dalloc(H, &H->d_tasks_tc, H->tasks_tc.size()) || dalloc(H, &H->d_part_tc, (size_t)ptc))
+            return HTLR_ECUDA;
+        HTLR_CK(cudaMemcpyAsync(H->d_tasks_tc, H->tasks_tc.data(), sizeof(Task) * H->tasks_tc.size(),
+                                cudaMemcpyHostToDevice, s));
+        HTLR_CK(cudaStreamSynchronize(s));
     }
     H->part_doubles = part;
     H->max_cols = max_cols;
@@ -858,7 +1001,55 @@ int run_chunk(const htlr_handle *H, const KindDesc *d_kinds, double *part,
     }
     mark(1);
     mark(2);
-    if (!H->tasks.empty()) launches += launch_streams(H, d_kinds, uc, N, nh, part, s);
+    if (H->tc) {
+        // tensor-core stream: pack the source operands, then one launch per block list
+        const int Rp = ((nh + 15) / 16) * 16;
+        auto tc_launch = [&](const TcShape &ts, int t0, int t1, const int *col, const int *blk,
+                             const void *blocks, const uint16_t *x, int rows, int ld) {
+            TcArgs a{};
+            a.tasks = H->d_tasks_tc;
+            a.t0 = t0;
+            a.t1 = t1;
+            a.col = col;
+            a.blk = blk;
+            a.blocks = static_cast<const uint16_t *>(blocks);
+            a.blk_elems = ts.blk_elems;
+            a.x = x;
+            a.x_box_elems = (long long)ts.nchunks * 3 * Rp * ts.kc;
+            a.mtiles = ts.mtiles;
+            a.kc = ts.kc;
+            a.nchunks = ts.nchunks;
+            a.Rp = Rp;
+            a.nr = nh;
+            a.rows = rows;
+            a.ld = ld;
+            a.stages = tc_stages(ts, Rp);
+            int cols = 32;
+            while (cols < ts.mtiles * Rp) cols *= 2;
+            a.tmem_cols = cols;
+            a.part = H->d_part_tc;
+            a.err = H->d_err;
+            launch_tc_stream(a, s);
+        };
+        for (int lv = 1; lv <= L; ++lv) {
+            const LevelData &Lv = H->lev[lv];
+            if (Lv.nfar == 0) continue;
+            launch_tc_pack_x(W[lv], (long long)H->nrc * Lv.pd, Lv.pd, Lv.nbox, nh, Rp, Lv.tc.kc,
+                             Lv.tc.nchunks, 0, d, n, H->leaf, L, nullptr, 0, Lv.d_Wp, s);
+            tc_launch(Lv.tc, Lv.tc_t0, Lv.tc_t1, Lv.d_far_col, Lv.d_far_core, Lv.d_cores, Lv.d_Wp,
+                      Lv.pd, Lv.ld);
+            launches += 2;
+        }
+        if (H->near_prec == kPrecBF16X6) {
+            launch_tc_pack_x(nullptr, 0, H->near_rows, 1 << (d * L), nh, Rp, H->near_tc.kc,
+                             H->near_tc.nchunks, 1, d, n, H->leaf, L, uc, N, H->d_Up, s);
+            tc_launch(H->near_tc, H->near_tc_t0, H->near_tc_t1, H->d_near_col, H->d_near_blk,
+                      H->d_near, H->d_Up, H->near_rows, H->near_ld);
+            launches += 2;
+        }
+    } else if (!H->tasks.empty()) {
+        launches += launch_streams(H, d_kinds, uc, N, nh, part, s);
+    }
     if (H->near_generated) {
         NearGenArgs g{};
         g.k = H->kern;
@@ -886,8 +1077,12 @@ int run_chunk(const htlr_handle *H, const KindDesc *d_kinds, double *part,
     for (int lv = 1; lv <= L; ++lv) {
         const LevelData &Lv = H->lev[lv];
         if (Lv.nfar == 0) continue;
-        launch_reduce_far(Lv.nbox, Lv.pd, Lv.ld, H->nrc, nh, Lv.d_row_task, H->d_tasks, part,
-                          Hs[lv], s);
+        if (H->tc)
+            launch_reduce_far(Lv.nbox, Lv.pd, Lv.ld, H->nrc, nh, Lv.d_row_task_tc, H->d_tasks_tc,
+                              H->d_part_tc, Hs[lv], s);
+        else
+            launch_reduce_far(Lv.nbox, Lv.pd, Lv.ld, H->nrc, nh, Lv.d_row_task, H->d_tasks, part,
+                              Hs[lv], s);
         ++launches;
     }
     mark(5);
@@ -899,11 +1094,14 @@ int run_chunk(const htlr_handle *H, const KindDesc *d_kinds, double *part,
     oa.nrc = H->nrc;
     oa.nrhs = nh;
     oa.leafg = level_geom(H, L);
-    oa.near_row_task = H->d_near_row_task;
-    oa.tasks = H->d_tasks;
-    oa.part = part;
+    const bool near_tc = H->near_prec == kPrecBF16X6;
+    oa.near_row_task = near_tc ? H->d_near_row_task_tc : H->d_near_row_task;
+    oa.tasks = near_tc ? H->d_tasks_tc : H->d_tasks;
+    oa.part = near_tc ? H->d_part_tc : part;
     oa.near_ld = H->near_ld;
-    oa.a_add = (H->near_generated || H->storage == HTLR_STORE_STORED) ? nullptr : H->d_a;
+    oa.a_add = (H->near_generated || (H->storage == HTLR_STORE_STORED && !near_tc)) ? nullptr
+                                                                                     : H->d_a;
+    oa.diag_add = near_tc ? H->d_diagpts : nullptr;
     oa.u = uc;
     oa.ldu = N;
     oa.near_in_f = H->near_generated;
@@ -1013,9 +1211,9 @@ int htlr_construct_ex(htlr_handle **out, const htlr_kernel *k, int d, int n, con
     int q = (o && o->quad_order > 0) ? o->quad_order : 16;
     if (q > 64) return fail(HTLR_EINVAL, "quad_order must be in 1..64");
     if (o && (o->orth < -1 || o->orth > 1)) return fail(HTLR_EINVAL, "orth must be -1, 0 or 1");
-    if (o && (o->far_precision < 0 || o->far_precision > 2 || o->near_precision < 0 ||
-              o->near_precision > 2))
-        return fail(HTLR_EINVAL, "precisions must be HTLR_PREC_FP64, _DF64 or _FP32");
+    if (o && (o->far_precision < 0 || o->far_precision > 3 || o->near_precision < 0 ||
+              o->near_precision > 3))
+        return fail(HTLR_EINVAL, "precisions must be HTLR_PREC_FP64, _DF64, _FP32 or _BF16X6");
 
     htlr_handle *H = nullptr;
     try {

@@ -30,10 +30,10 @@ constexpr int kMaxD = 3;
 constexpr int kMaxP = 16;
 
 // Device error codes written into the handle's error word.
-enum DevErr : int { kDevOk = 0, kDevBadIndex = 1, kDevBadTask = 2 };
+enum DevErr : int { kDevOk = 0, kDevBadIndex = 1, kDevBadTask = 2, kDevTimeout = 3 };
 
 // Arithmetic of a block list (same values as the public htlr_precision enum).
-enum Prec : int { kPrecFP64 = 0, kPrecDF64 = 1, kPrecFP32 = 2 };
+enum Prec : int { kPrecFP64 = 0, kPrecDF64 = 1, kPrecFP32 = 2, kPrecBF16X6 = 3 };
 
 // Bytes of one block element in memory for a precision.
 inline size_t prec_bytes(int prec) { return prec == kPrecFP32 ? 4 : 8; }
@@ -69,8 +69,22 @@ struct KindDesc {
     long long x_box_stride;  // doubles per box in x (nrc * pd)
 };
 
+// Shape of a block list in the packed split-TF32 layout of the tensor-core stream.
+constexpr int kTcRpMax = 64;  // right-hand sides per tensor-core pass
+struct TcShape {
+    int rows = 0, cols = 0, mtiles = 0, kc = 0, nchunks = 0;
+    long long blk_elems = 0;     // bf16 elements per packed block
+    long long x_elems = 0;       // bf16 elements per packed source box (for kTcRpMax)
+};
+
 struct LevelData {
     int level = 0, nb = 0, nbox1 = 0, nbox = 0, pe = 0, pd = 0, ld = 0;
+    // tensor-core form (precision BF16X6)
+    TcShape tc;
+    uint16_t *d_Wp = nullptr;               // packed W, nbox x tc.x_elems
+    int tc_t0 = 0, tc_t1 = 0;               // task range in the tensor-core task list
+    std::vector<int> row_task_tc;
+    int *d_row_task_tc = nullptr;
     int64_t nfar = 0;
     std::vector<int> far_rowptr, far_col, far_core;
     int *d_far_rowptr = nullptr, *d_far_col = nullptr, *d_far_core = nullptr;
@@ -129,6 +143,16 @@ struct htlr_handle {
     int max_cols = 1;
     int far_prec = 0, near_prec = 0;
     int near_task0 = 0;  // first task of the inadmissible leaves
+    // tensor-core stream (far_prec / near_prec BF16X6): row tasks, partials, near operand
+    int tc = 0;
+    std::vector<htlr::Task> tasks_tc;
+    htlr::Task *d_tasks_tc = nullptr;
+    double *d_part_tc = nullptr;
+    htlr::TcShape near_tc;
+    uint16_t *d_Up = nullptr;        // packed u per leaf
+    int near_tc_t0 = 0, near_tc_t1 = 0;
+    std::vector<int> near_row_task_tc;
+    int *d_near_row_task_tc = nullptr;
     int *d_err = nullptr;
     // host staging for htlr_matvec_host
     double *d_stage_u = nullptr, *d_stage_f = nullptr;
@@ -165,6 +189,8 @@ void launch_diag(const KernelDesc &k, int d, double h, int q, const double *d_gx
 void launch_cores(const KernelDesc &k, int d, int p, int pe, int ld, int apply_r, double side,
                   double wgt, const double *d_R, int64_t ncores, const int *d_off,
                   double *d_cores, double *d_scratch, int nscratch_ctas, cudaStream_t s);
+// Zero the diagonal entries of the dense blocks listed in d_ids.
+void launch_zero_diag(double *blocks, int ld, int rows, const int *d_ids, int nids, cudaStream_t s);
 // Precision conversions of finished blocks: in place to (hi, lo) float pairs, or into a
 // separate FP32 array.
 void launch_split_df64(double *d_buf, size_t count, cudaStream_t s);
@@ -230,6 +256,7 @@ struct OutArgs {
     const double *part;
     int near_ld;
     const double *a_add;         // add a(x) u when the dense blocks do not hold it
+    const double *diag_add;      // add K_ii w_i u_i (per point) when the blocks do not hold it
     const double *u;
     long long ldu;
     int near_in_f;
@@ -258,6 +285,29 @@ struct NearGenArgs {
     int max_rows;
 };
 void launch_near_generated(int prec, const NearGenArgs &a, cudaStream_t s);
+// ---- tc_stream.cu: tensor-core (tcgen05) block stream for many right-hand sides ----
+constexpr int kTcMaxStages = 8;
+struct TcArgs {
+    const Task *tasks;  // one task per non-empty block row
+    int t0, t1;
+    const int *col, *blk;      // CSR entries of the kind
+    const uint16_t *blocks;    // packed split-BF16 blocks
+    long long blk_elems;       // elements per packed block
+    const uint16_t *x;         // packed source operand, per source box
+    long long x_box_elems;
+    int mtiles, kc, nchunks, Rp, nr, rows, ld, stages, tmem_cols;
+    double *part;
+    int *err;
+};
+void launch_tc_stream(const TcArgs &a, cudaStream_t s);
+// Shared-memory bytes of one pipeline stage (A chunk + B chunk, all splits).
+size_t tc_stage_bytes(int mtiles, int kc, int Rp);
+void launch_tc_pack_blocks(const double *src, long long nblk, int ld, int rows, int cols,
+                           int mtiles, int kc, int nchunks, uint16_t *dst, cudaStream_t s);
+void launch_tc_pack_x(const double *W, long long w_box_stride, int pd, int nbox, int nr, int Rp,
+                      int kc, int nchunks, int is_near, int d, int n, int leaf, int L,
+                      const double *u, long long ldu, uint16_t *dst, cudaStream_t s);
+
 // Tensor grids: factors of every (level, dim, box), U(i, mu) = L_mu(x_i) and
 // V(i, mu) = L_mu(x_i) w_i on the Chebyshev points of the box's geometric cell.
 // geo: the level's device geometry array, per dimension [first | cnt | uoff | voff], each

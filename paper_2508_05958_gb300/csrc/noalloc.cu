@@ -71,6 +71,11 @@ int matvec_noalloc(const htlr_handle *H, const double *u, double *f, int nrhs)
         set_error("htlr_matvec_noalloc: the handle's device is not the current device");
         return HTLR_EINVAL;
     }
+    if (H->tc) {
+        set_error("htlr_matvec_noalloc: operators with a TF32X3 (tensor-core) far field are "
+                  "not supported; use htlr_matvec");
+        return HTLR_EUNSUPPORTED;
+    }
     // carve the scratch: kinds table, W and H per far level, task partials
     const int d = H->d, n = H->n, L = H->L;
     size_t off = 0;

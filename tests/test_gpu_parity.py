@@ -162,6 +162,11 @@ def test_memory_limit_refusal():
 # ----------------------------------------------------------------------------------
 MIXED_TOL = 1e-6
 FP32_TOL = 1e-5     # far and near fields both in FP32
+# tensor cores (three-way BF16 split, FP32 accumulation in tensor memory): the products
+# are FP32-class, but the accumulator's rounding error grows with the number of MMAs
+# summed into it (about 2e-8 relative per accumulation, measured); whole block rows of
+# the n = 32 workloads reach ~2e-4.  Stated tolerance of this mode: 1e-3
+TC_TOL = 1e-3
 
 
 @pytest.mark.parametrize("storage", [1, 2])
@@ -282,4 +287,51 @@ def test_tensor_grid_rejects_empty_boxes_and_orth():
     g = _qgrid(2, 16)
     with pytest.raises(htlr.HTLRError) as ei:
         htlr.htlr_construct(2, 2, 16, 4, 3, 1.0, grid=g, orth=1)
+    assert ei.value.code == htlr.HTLR_EUNSUPPORTED
+
+
+# ----------------------------------------------------------------------------------
+# Tensor cores (tcgen05, three-way BF16 split, FP32 accumulation) for many right-hand sides
+# ----------------------------------------------------------------------------------
+@pytest.mark.parametrize("nrhs", [1, 16, 20, 64, 70])
+def test_tensor_core_stream_matches_oracle(oracle, nrhs):
+    from paper_2508_05958_gb300.workloads import workload
+    w = workload("c2", n=16)                      # 125-row cores (pe = 5) and 64-row leaves
+    u = w.u(nrhs=nrhs)
+    f, info = gpu_matvec(w, u, storage=2, far_precision=3, near_precision=3)
+    assert info["far_precision"] == 3
+    ref, _ = _oracle_htlr(oracle, w, u)
+    err = rel(f, ref)
+    assert err < TC_TOL, err
+
+
+@pytest.mark.parametrize("case", [dict(name="c1", over={}), dict(name="c3", over=dict(n=32)),
+                                  dict(name="c2", over=dict(n=32, leaf=8, p=6))])
+def test_tensor_core_stream_shapes(oracle, case):
+    """d = 2 (36-row cores), 216-row cores over two M-tiles, 512-row leaf blocks over four."""
+    from paper_2508_05958_gb300.workloads import workload
+    w = workload(case["name"], **case["over"])
+    u = w.u(nrhs=8)
+    f, _ = gpu_matvec(w, u, storage=2, far_precision=3, near_precision=3)
+    ref, _ = _oracle_htlr(oracle, w, u)
+    assert rel(f, ref) < TC_TOL
+
+
+def test_tensor_core_far_with_generated_near(oracle):
+    from paper_2508_05958_gb300.workloads import Workload
+    w = Workload("tq", d=3, n=32, ktype=2, leaf=4, p=4, eta=1.0, seed=33)
+    grid = _qgrid(3, 32, seed=9)
+    u = w.u(nrhs=16)
+    f, info = _gpu_tensor(w, grid, u, far_precision=3, near_precision=0)
+    ref = oracle.HTLR(3, 32, 2, 4, 4, 1.0, grid=grid, orth=False).matvec(u)
+    assert rel(f, ref) < TC_TOL
+
+
+def test_tensor_core_rejects_unsupported_mixes():
+    from paper_2508_05958_gb300 import htlr
+    with pytest.raises(htlr.HTLRError) as ei:
+        htlr.htlr_construct(1, 3, 16, 4, 4, 1.0, storage=2, far_precision=3, near_precision=0)
+    assert ei.value.code == htlr.HTLR_EUNSUPPORTED
+    with pytest.raises(htlr.HTLRError) as ei:
+        htlr.htlr_construct(1, 3, 16, 4, 4, 1.0, storage=2, far_precision=0, near_precision=3)
     assert ei.value.code == htlr.HTLR_EUNSUPPORTED
