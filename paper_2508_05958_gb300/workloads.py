@@ -125,6 +125,10 @@ CONFIGS = {
                         a_kind="sin", u_kind="normal", seed=2),
     "c4": Workload("c4", d=3, n=128, ktype=K_EXP_R, leaf=8, p=7, eta=1.0, nrhs=16,
                    a_kind="zero", u_kind="normal", grid_kind="quasi", seed=4),
+    # the c3 operator one level shallower (N = 262144, 64 RHS): the same core and near
+    # block shapes (216 x 216, 512 x 512) with ~0.3 GB of vectors, for profiling captures
+    "c3_n64": Workload("c3_n64", d=3, n=64, ktype=K_INV_R, leaf=8, p=6, eta=1.0, nrhs=64,
+                       a_kind="zero", u_kind="normal", seed=3),
 }
 
 
