@@ -46,6 +46,11 @@ def parse():
     ap.add_argument("--gmres-solves", type=int, default=20,
                     help="GMRES solves (to 1e-10) timed after the matvec, per variant")
     ap.add_argument("--cpu-sample-s", type=float, default=20.0)
+    ap.add_argument("--serve-requests", type=int, default=120,
+                    help="requests of the Poisson serving stream (0: skip serving)")
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-max-n2", type=int, default=512)
+    ap.add_argument("--serve-max-n3", type=int, default=64)
     return ap.parse_args()
 
 
@@ -346,6 +351,36 @@ def time_gmres(w, solves, stream):
     return out
 
 
+def time_serving(args):
+    """Continuous-batching solve server against FP64 one-at-a-time on the same seeded
+    Poisson stream of GMRES(30) solves to 1e-10 (operators warmed: one solve each first)."""
+    from paper_2508_05958_gb300 import htlr, serving
+    ops = serving.family(max_n2=args.serve_max_n2, max_n3=args.serve_max_n3)
+    stream = serving.request_stream(ops, args.serve_rate, args.serve_requests, seed=2025)
+    arms = {"fp64_one_at_a_time": dict(mixed=0, max_active=1, max_batch=1),
+            "mixed_batched": dict(mixed=1, inner_precision=htlr.PREC_FP32, max_active=64,
+                                  max_batch=16)}
+    out = {"workload": f"{len(ops)} operators (d=2 n<={args.serve_max_n2} log; d=3 "
+                       f"n<={args.serve_max_n3} 1/r, exp(-r); r in 5..7; SHARED), "
+                       f"{args.serve_requests} requests, Poisson {args.serve_rate:g}/s, "
+                       "f ~ N(0,1), GMRES(30) to 1e-10"}
+    for name, kw in arms.items():
+        with htlr.Server(**kw) as S:
+            ids = [S.add_operator(o.ktype, o.d, o.n, o.leaf, o.r, o.eta, a=o.a(), storage=2)
+                   for o in ops]
+            for k, o in enumerate(ops):                 # warm: construct every operator
+                S.wait(S.submit(ids[k], serving.rhs(o, 1)))
+            res = serving.replay(S, ops, stream, op_ids=ids)
+            st = S.stats()
+        res["batched_matvecs"] = st["batched_matvecs"]
+        res["mean_columns_per_matvec"] = st["matvec_columns"] / max(1, st["batched_matvecs"])
+        res["max_batch_seen"] = st["max_batch_seen"]
+        out[name] = res
+    out["solves_per_s_ratio"] = (out["mixed_batched"]["solves_per_s"] /
+                                 out["fp64_one_at_a_time"]["solves_per_s"])
+    return out
+
+
 def run_gpu(args, w):
     import torch
     from paper_2508_05958_gb300 import htlr
@@ -455,6 +490,8 @@ def run_gpu(args, w):
     }
     if args.gmres_solves > 0 and w.a_kind != "zero":
         line["gmres"] = time_gmres(w, args.gmres_solves, stream)
+    if args.serve_requests > 0 and world == 1:
+        line["serving"] = time_serving(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         val, cores, sample, _ = time_oracle(w, args.cpu_sample_s)
         line["cpu_baseline"] = {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",

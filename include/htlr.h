@@ -242,6 +242,142 @@ typedef struct {
 int htlr_gmres(const htlr_handle *H, const htlr_handle *H_inner, const double *f, double *u,
                int nrhs, const htlr_gmres_options *o, htlr_gmres_result *res);
 
+/*
+ * Matvec plans (no counterpart in the paper): the launch sequence of one htlr_matvec
+ * (H, u, f, nrhs) captured once into a CUDA graph and replayed by one graph launch, for
+ * callers that apply an operator many times to the same device buffers (iterative
+ * solvers, serving loops).  u and f are fixed at creation: the caller rewrites their
+ * contents between launches.  The plan borrows H (free plans before H).
+ *   htlr_plan_create  captures on a private stream; errors as htlr_matvec.
+ *   htlr_plan_launch  enqueues f = A u on the handle's current stream; if H's task tables
+ *                     were rebuilt since the capture (htlr_autotune) it re-captures first.
+ *   htlr_plan_launches  the kernel launches inside the graph (-1 for NULL).
+ *   htlr_plan_free    releases the graph; NULL is a no-op.
+ */
+typedef struct htlr_plan htlr_plan;
+int htlr_plan_create(const htlr_handle *H, const double *u, double *f, int nrhs,
+                     htlr_plan **P);
+int htlr_plan_launch(htlr_plan *P);
+int htlr_plan_launches(const htlr_plan *P);
+void htlr_plan_free(htlr_plan *P);
+
+/* Launch shapes chosen by htlr_autotune. */
+typedef struct {
+    size_t task_bytes;       /* CUDA-core block stream: bytes of blocks per warp task */
+    int stream_ctas_per_sm;  /* CUDA-core block stream: grid cap = 152 x this */
+    int stream_threads;      /* CUDA-core block stream: threads per CTA (128 or 256) */
+    int tc_stages;           /* tensor-core ring depth cap (0: the deepest that fits) */
+    float ms;                /* median matvec time of the chosen shapes (ms; 0 if cached) */
+    float default_ms;        /* median matvec time of the shapes the handle had before */
+    int candidates;          /* configurations timed */
+    int from_cache;          /* 1: taken from the process-wide table, nothing timed */
+} htlr_tune_result;
+
+/*
+ * htlr_autotune -- choose the matvec's launch shapes for nrhs right-hand sides by timing
+ * (no counterpart in the paper).  Coordinate descent from the handle's current shapes:
+ * the stream's task size (64 KB .. 1 MB of blocks per warp task), its grid cap (2..16
+ * CTAs per SM) and CTA size (128 / 256), or the tensor-core ring depth (2..4); each
+ * candidate is the median of 3 matvecs (CUDA events, handle's stream) after a warm-up, on
+ * scratch vectors the call allocates (2 N nrhs doubles).  Stops trying candidates when
+ * the next one would exceed budget_ms of device time (0: time only the current shapes).
+ * The winner is applied to H and stored in a process-wide table keyed by the operator's
+ * shape (d, n, leaf, r, eta, storage, precisions, kernel, min(nrhs, RHS chunk)); a later
+ * call for the same shape applies it without timing.  Results change only by rounding
+ * order.  Plans captured on H re-capture on their next launch.  Synchronous.
+ */
+int htlr_autotune(htlr_handle *H, int nrhs, double budget_ms, htlr_tune_result *res);
+
+/* Forget every shape htlr_autotune remembered. */
+void htlr_autotune_clear_cache(void);
+
+/* ---------------------------------------------------------------------------------
+ * Serving loop (no counterpart in the paper): a request loop that keeps constructed
+ * operators resident and solves a(x) u + K u = f for many concurrent requests with
+ * continuous batching.  A scheduler thread owns the device: requests wait in a FIFO
+ * until a slot (max_active) and HBM are free; an operator is constructed (Algorithm 1)
+ * when a request first needs it and released, least recently used first, when an idle
+ * one is in the way of a new one.  Each active request is a restarted GMRES(restart)
+ * solve (FP64 Arnoldi with classical Gram-Schmidt twice, Givens rotations); every
+ * scheduler step applies each operator once to the columns of all its requests that
+ * need it (at most max_batch), so requests arriving while others iterate join the next
+ * step, and converged ones leave at once.  Operators run on their own streams and their
+ * steps overlap on the device.  Mixed mode: each operator has a df64 handle that defines
+ * the residual and an inner handle (inner_precision) that builds the Krylov spaces, and
+ * each restart is a step of iterative refinement (each inner cycle stops at inner_tol
+ * times its starting residual).  A result does not depend on which requests shared its
+ * batches: every column of a batched matvec and every per-request reduction is computed
+ * as it would be alone.
+ * --------------------------------------------------------------------------------- */
+typedef struct htlr_server htlr_server;
+
+typedef struct {
+    size_t hbm_budget;    /* device bytes for resident operators, batch buffers and request
+                             workspaces ((restart + 4) N doubles each); 0: 80% of free */
+    int max_active;       /* requests iterating at once (slots), >= 1 */
+    int max_batch;        /* columns per batched matvec, 1..64 */
+    int mixed;            /* 0: FP64 operators; 1: df64 residual + inner operator */
+    int inner_precision;  /* mixed: HTLR_PREC_FP32, _DF64 or _BF16X6 (far and near) */
+    int restart;          /* GMRES restart length, 1..200 */
+    double tol;           /* target ||f - A u|| / ||f|| (A: the FP64 or df64 operator) */
+    double inner_tol;     /* mixed: relative residual reduction of each inner cycle, (0,1) */
+    int max_iters;        /* Arnoldi steps per request, over all restarts */
+    int use_graphs;       /* 1: batched matvecs replayed from captured plans (htlr_plan) */
+    double autotune_ms;   /* > 0: htlr_autotune budget for each constructed handle */
+} htlr_server_options;
+
+typedef struct {          /* one operator of the served family (uniform grid, orth default) */
+    int kernel_type;      /* htlr_kernel_type */
+    double kscale, kparam;
+    int d, n, leaf, r;
+    double eta;
+    const double *a;      /* host array of N values (natural order) or NULL (a = 0); copied */
+    int storage;          /* htlr_storage: AUTO, STORED or SHARED */
+} htlr_operator_spec;
+
+enum { HTLR_REQ_QUEUED = 0, HTLR_REQ_ACTIVE = 1, HTLR_REQ_DONE = 2, HTLR_REQ_FAILED = 3 };
+
+typedef struct {
+    int status;           /* HTLR_REQ_* */
+    int error;            /* HTLR_* code when failed */
+    int iterations;       /* Arnoldi steps */
+    int matvecs;          /* operator applications (columns of batched matvecs) */
+    int refinements;      /* mixed: correction steps after the first */
+    double rel_residual;  /* ||f - A u|| / ||f|| at the last residual check */
+    int converged;        /* rel_residual <= tol */
+    double submit_s, admit_s, done_s;  /* seconds since the server was created */
+} htlr_request_info;
+
+typedef struct {
+    long long submitted, completed, failed;
+    int active, pending;
+    long long steps, batched_matvecs, matvec_columns;
+    int max_batch_seen;
+    long long constructions, evictions;
+    long long bytes_in_use, bytes_peak, bytes_budget;
+    int resident_operators;
+} htlr_server_stats;
+
+/* Start a server on the current device (o NULL: max_active 64, max_batch 16, mixed 1
+ * with FP32 inner, restart 30, tol 1e-10, inner_tol 1e-4, max_iters 3000, graphs on,
+ * no autotuning, budget 80% of free memory).  HTLR_EINVAL for bad options. */
+int htlr_server_create(const htlr_server_options *o, htlr_server **S);
+/* Register an operator (constructed on first use); *op_id names it in submissions. */
+int htlr_server_add_operator(htlr_server *S, const htlr_operator_spec *spec, int *op_id);
+/* Queue the solve of A u = f for operator op_id.  f_host (N doubles) is copied before the
+ * call returns; u_host (N doubles, host) receives the solution and must stay valid until
+ * the request is DONE or FAILED.  Thread-safe. */
+int htlr_server_submit(htlr_server *S, int op_id, const double *f_host, double *u_host,
+                       long long *req_id);
+/* Current state of a request (non-blocking). */
+int htlr_server_poll(htlr_server *S, long long req_id, htlr_request_info *info);
+/* Block until the request is DONE or FAILED (timeout_s < 0: no limit; HTLR_ETIMEOUT). */
+int htlr_server_wait(htlr_server *S, long long req_id, double timeout_s, htlr_request_info *info);
+/* Counters and memory use. */
+int htlr_server_get_stats(htlr_server *S, htlr_server_stats *st);
+/* Finish every queued and active request, release all operators and stop the thread. */
+void htlr_server_destroy(htlr_server *S);
+
 /* Release everything the handle owns.  NULL is a no-op.  A second free of the same
  * handle is detected through a magic word and ignored (reported by htlr_last_error). */
 void htlr_free(htlr_handle *H);

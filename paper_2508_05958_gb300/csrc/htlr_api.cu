@@ -55,6 +55,20 @@ static int dalloc(htlr_handle *H, T **p, size_t count)
     return HTLR_OK;
 }
 
+// Release one allocation made by dalloc (and forget it).
+template <class T>
+static void dfree(htlr_handle *H, T *&p)
+{
+    if (!p) return;
+    for (size_t i = 0; i < H->allocs.size(); ++i)
+        if (H->allocs[i] == (void *)p) {
+            H->allocs.erase(H->allocs.begin() + (long)i);
+            break;
+        }
+    cudaFree((void *)p);
+    p = nullptr;
+}
+
 // Scratch allocations released at the end of construction.
 struct Temps {
     std::vector<void *> p;
@@ -155,6 +169,88 @@ static int tc_stages(const TcShape &t, int Rp)
     int S = (int)((210 * 1024) / tc_stage_bytes(t.mtiles, t.kc, Rp));
     if (S > kTcMaxStages) S = kTcMaxStages;
     return S < 2 ? 2 : S;
+}
+
+// CUDA-core stream tasks: runs of consecutive entries of one block row holding about
+// `task_bytes` of blocks each (at least one entry), a partial-sum slot of nrc x ld
+// doubles per task, and per row the index of its first task (the reductions sum a row's
+// partials in task order).  Rebuilt in place by the autotuner; device tables are
+// replaced and `generation` moves on.
+int build_tasks(htlr_handle *H, size_t task_bytes, cudaStream_t s)
+{
+    const int d = H->d, L = H->L;
+    const int rows_leaf = (int)ipow(H->leaf, d);
+    std::vector<Task> tasks;
+    long long part = 0;
+    auto make_tasks = [&](int kind, const std::vector<int> &rowptr, int nrows, size_t blk_bytes,
+                          int ld, std::vector<int> &row_task) {
+        long long per = std::max<long long>(1, (long long)(task_bytes / blk_bytes));
+        row_task.assign(nrows + 1, 0);
+        for (int t = 0; t < nrows; ++t) {
+            row_task[t] = (int)tasks.size();
+            for (long long e = rowptr[t]; e < rowptr[t + 1]; e += per) {
+                Task T;
+                T.kind = kind;
+                T.row = t;
+                T.e0 = (int)e;
+                T.e1 = (int)std::min<long long>(rowptr[t + 1], e + per);
+                T.part = part;
+                part += (long long)H->nrc * ld;
+                tasks.push_back(T);
+            }
+        }
+        row_task[nrows] = (int)tasks.size();
+    };
+    for (int lv = 1; lv <= L; ++lv) {
+        LevelData &Lv = H->lev[lv];
+        if (Lv.nfar == 0) continue;
+        if (H->tc)
+            Lv.row_task_begin.assign(Lv.nbox + 1, (int)tasks.size());  // no CUDA-core tasks
+        else
+            make_tasks(lv, Lv.far_rowptr, Lv.nbox, (size_t)Lv.ld * Lv.pd * prec_bytes(H->far_prec),
+                       Lv.ld, Lv.row_task_begin);
+    }
+    const int near_task0 = (int)tasks.size();
+    if (!H->near_generated) {
+        if (H->near_prec == kPrecBF16X6)
+            H->near_row_task.assign((1 << (d * L)) + 1, (int)tasks.size());
+        else
+            make_tasks(L + 1, H->near_rowptr, 1 << (d * L),
+                       (size_t)H->near_ld * rows_leaf * prec_bytes(H->near_prec), H->near_ld,
+                       H->near_row_task);
+    }
+    // replace the device tables
+    HTLR_CK(cudaStreamSynchronize(s));
+    HTLR_CK(cudaStreamSynchronize(H->stream));
+    for (int lv = 1; lv <= L; ++lv) {
+        LevelData &Lv = H->lev[lv];
+        if (Lv.nfar == 0) continue;
+        dfree(H, Lv.d_row_task);
+        if (dalloc(H, &Lv.d_row_task, Lv.row_task_begin.size())) return HTLR_ECUDA;
+        HTLR_CK(cudaMemcpyAsync(Lv.d_row_task, Lv.row_task_begin.data(),
+                                sizeof(int) * Lv.row_task_begin.size(), cudaMemcpyHostToDevice, s));
+    }
+    if (!H->near_generated) {
+        dfree(H, H->d_near_row_task);
+        if (dalloc(H, &H->d_near_row_task, H->near_row_task.size())) return HTLR_ECUDA;
+        HTLR_CK(cudaMemcpyAsync(H->d_near_row_task, H->near_row_task.data(),
+                                sizeof(int) * H->near_row_task.size(), cudaMemcpyHostToDevice, s));
+    }
+    if (part > H->part_doubles || !H->d_part) {
+        dfree(H, H->d_part);
+        if (dalloc(H, &H->d_part, (size_t)part)) return HTLR_ECUDA;
+        H->part_doubles = part;
+    }
+    dfree(H, H->d_tasks);
+    if (dalloc(H, &H->d_tasks, tasks.size())) return HTLR_ECUDA;
+    HTLR_CK(cudaMemcpyAsync(H->d_tasks, tasks.data(), sizeof(Task) * tasks.size(),
+                            cudaMemcpyHostToDevice, s));
+    HTLR_CK(cudaStreamSynchronize(s));
+    H->tasks.swap(tasks);
+    H->near_task0 = near_task0;
+    H->task_bytes = task_bytes;
+    ++H->generation;
+    return HTLR_OK;
 }
 
 static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
@@ -728,39 +824,12 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
         HTLR_CK(cudaStreamSynchronize(s));
     }
 
-    // ---- task list and kinds ----
+    // ---- kinds (block lists per level + the near list); tasks follow ----
     H->kinds.assign(L + 2, KindDesc{});
-    H->tasks.clear();
-    long long part = 0;
-    auto make_tasks = [&](int kind, const std::vector<int> &rowptr, int nrows, size_t blk_bytes,
-                          int ld, std::vector<int> &row_task) {
-        long long per = std::max<long long>(1, (long long)(kTaskBytes / blk_bytes));
-        row_task.assign(nrows + 1, 0);
-        for (int t = 0; t < nrows; ++t) {
-            row_task[t] = (int)H->tasks.size();
-            for (long long e = rowptr[t]; e < rowptr[t + 1]; e += per) {
-                Task T;
-                T.kind = kind;
-                T.row = t;
-                T.e0 = (int)e;
-                T.e1 = (int)std::min<long long>(rowptr[t + 1], e + per);
-                T.part = part;
-                part += (long long)H->nrc * ld;
-                H->tasks.push_back(T);
-            }
-        }
-        row_task[nrows] = (int)H->tasks.size();
-    };
     int max_cols = 1;
     for (int lv = 1; lv <= L; ++lv) {
         LevelData &Lv = H->lev[lv];
         if (Lv.nfar == 0) continue;
-        if (H->tc) {
-            Lv.row_task_begin.assign(Lv.nbox + 1, (int)H->tasks.size());  // no CUDA-core tasks
-        } else {
-            make_tasks(lv, Lv.far_rowptr, Lv.nbox, (size_t)Lv.ld * Lv.pd * prec_bytes(H->far_prec),
-                       Lv.ld, Lv.row_task_begin);
-        }
         KindDesc &K = H->kinds[lv];
         K.col = Lv.d_far_col;
         K.blk = Lv.d_far_core;
@@ -775,18 +844,8 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
         K.x = Lv.d_W;
         K.x_box_stride = (long long)H->nrc * Lv.pd;
         max_cols = std::max(max_cols, Lv.pd);
-        if (dalloc(H, &Lv.d_row_task, Lv.row_task_begin.size())) return HTLR_ECUDA;
-        HTLR_CK(cudaMemcpyAsync(Lv.d_row_task, Lv.row_task_begin.data(),
-                                sizeof(int) * Lv.row_task_begin.size(), cudaMemcpyHostToDevice, s));
     }
-    H->near_task0 = (int)H->tasks.size();
     if (!H->near_generated) {
-        if (H->near_prec == kPrecBF16X6)
-            H->near_row_task.assign((1 << (d * L)) + 1, (int)H->tasks.size());
-        else
-            make_tasks(L + 1, H->near_rowptr, 1 << (d * L),
-                       (size_t)H->near_ld * rows_leaf * prec_bytes(H->near_prec), H->near_ld,
-                       H->near_row_task);
         KindDesc &K = H->kinds[L + 1];
         K.col = H->d_near_col;
         K.blk = H->d_near_blk;
@@ -801,9 +860,6 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
         K.x = nullptr;
         K.x_box_stride = 0;
         max_cols = std::max(max_cols, rows_leaf);
-        if (dalloc(H, &H->d_near_row_task, H->near_row_task.size())) return HTLR_ECUDA;
-        HTLR_CK(cudaMemcpyAsync(H->d_near_row_task, H->near_row_task.data(),
-                                sizeof(int) * H->near_row_task.size(), cudaMemcpyHostToDevice, s));
     }
     // tensor-core stream: one task per non-empty block row, partials for kTcRpMax RHS
     if (H->tc) {
@@ -855,13 +911,10 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
                                 cudaMemcpyHostToDevice, s));
         HTLR_CK(cudaStreamSynchronize(s));
     }
-    H->part_doubles = part;
     H->max_cols = max_cols;
-    if (dalloc(H, &H->d_part, (size_t)part) || dalloc(H, &H->d_tasks, H->tasks.size()) ||
-        dalloc(H, &H->d_kinds, H->kinds.size()))
-        return HTLR_ECUDA;
-    HTLR_CK(cudaMemcpyAsync(H->d_tasks, H->tasks.data(), sizeof(Task) * H->tasks.size(),
-                            cudaMemcpyHostToDevice, s));
+    H->task_bytes = kTaskBytes;
+    if (int rc = build_tasks(H, kTaskBytes, s)) return rc;
+    if (dalloc(H, &H->d_kinds, H->kinds.size())) return HTLR_ECUDA;
     HTLR_CK(cudaMemcpyAsync(H->d_kinds, H->kinds.data(), sizeof(KindDesc) * H->kinds.size(),
                             cudaMemcpyHostToDevice, s));
     HTLR_CK(cudaStreamSynchronize(s));
@@ -943,6 +996,8 @@ int launch_streams(const htlr_handle *H, const KindDesc *d_kinds, const double *
     a.err = H->d_err;
     a.streaming = H->storage == HTLR_STORE_STORED;
     a.stream = s;
+    a.threads = H->stream_threads;
+    a.ctas_per_sm = H->stream_ctas_per_sm;
     const int nt = (int)H->tasks.size();
     if (H->far_prec == H->near_prec) {
         a.t0 = 0;
@@ -1024,6 +1079,7 @@ int run_chunk(const htlr_handle *H, const KindDesc *d_kinds, double *part,
             a.rows = rows;
             a.ld = ld;
             a.stages = tc_stages(ts, Rp);
+            if (H->tc_stages_cap >= 2 && a.stages > H->tc_stages_cap) a.stages = H->tc_stages_cap;
             int cols = 32;
             while (cols < ts.mtiles * Rp) cols *= 2;
             a.tmem_cols = cols;
@@ -1128,7 +1184,7 @@ int run_chunk(const htlr_handle *H, const KindDesc *d_kinds, double *part,
 }
 
 static int enqueue_matvec(const htlr_handle *H, const double *u, double *f, int nrhs,
-                          StageEvents *tev = nullptr);
+                          StageEvents *tev = nullptr, cudaStream_t on = nullptr);
 
 // HMultVec for other parts of the library (GMRES): enqueue on the handle's stream.
 int matvec_enqueue(const htlr_handle *H, const double *u, double *f, int nrhs)
@@ -1136,9 +1192,16 @@ int matvec_enqueue(const htlr_handle *H, const double *u, double *f, int nrhs)
     return enqueue_matvec(H, u, f, nrhs);
 }
 
-static int enqueue_matvec(const htlr_handle *H, const double *u, double *f, int nrhs,
-                          StageEvents *tev)
+// The same sequence of launches on another stream (graph capture).
+int matvec_enqueue_on(const htlr_handle *H, const double *u, double *f, int nrhs, cudaStream_t s)
 {
+    return enqueue_matvec(H, u, f, nrhs, nullptr, s);
+}
+
+static int enqueue_matvec(const htlr_handle *H, const double *u, double *f, int nrhs,
+                          StageEvents *tev, cudaStream_t on)
+{
+    cudaStream_t st = on ? on : H->stream;
     const long long N = (long long)ipow(H->n, H->d);
     std::vector<double *> W(H->L + 1, nullptr), Hs(H->L + 1, nullptr);
     for (int lv = 1; lv <= H->L; ++lv) {
@@ -1149,7 +1212,7 @@ static int enqueue_matvec(const htlr_handle *H, const double *u, double *f, int 
     for (int c0 = 0; c0 < nrhs; c0 += H->nrc) {
         const int nh = std::min(H->nrc, nrhs - c0);
         launches += run_chunk(H, H->d_kinds, H->d_part, W, Hs, u + (long long)c0 * N,
-                              f + (long long)c0 * N, nh, tev, H->stream);
+                              f + (long long)c0 * N, nh, tev, st);
     }
     const_cast<htlr_handle *>(H)->last_launches = launches;
     cudaError_t e = cudaGetLastError();

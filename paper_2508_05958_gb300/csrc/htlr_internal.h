@@ -158,6 +158,12 @@ struct htlr_handle {
     double *d_stage_u = nullptr, *d_stage_f = nullptr;
     size_t stage_cap = 0;
     int last_launches = 0;
+    // launch tuning (autotuner): stream task size, CUDA-core stream CTAs per SM and
+    // threads per CTA, tensor-core ring depth (0 = largest that fits); `generation`
+    // changes whenever the device-side task tables are rebuilt (captured plans re-capture)
+    size_t task_bytes = 256 * 1024;
+    int stream_ctas_per_sm = 8, stream_threads = 256, tc_stages_cap = 0;
+    int generation = 0;
     htlr_stats stats{};
     std::vector<void *> allocs;
 };
@@ -217,11 +223,15 @@ struct StreamArgs {
     int *err;
     bool streaming;
     cudaStream_t stream;
+    int threads = 256;     // 128 or 256 (one warp per task)
+    int ctas_per_sm = 8;   // grid cap: 152 x ctas_per_sm
 };
 void launch_stream_fp64(const StreamArgs &a);
 void launch_stream_df64(const StreamArgs &a);
 void launch_stream_fp32(const StreamArgs &a);
 void launch_stream(int prec, const StreamArgs &a);
+// (Re)build the CUDA-core stream tasks of H for a task size in bytes (htlr_api.cu).
+int build_tasks(htlr_handle *H, size_t task_bytes, cudaStream_t s);
 // Level of the leaves: n = leaf * 2^nl_level.
 int leaf_level(int n, int leaf);
 void launch_reduce_far(int nbox, int pd, int ld, int nrc, int nrhs_here, const int *d_row_task,

@@ -72,7 +72,7 @@ int matvec_noalloc(const htlr_handle *H, const double *u, double *f, int nrhs)
         return HTLR_EINVAL;
     }
     if (H->tc) {
-        set_error("htlr_matvec_noalloc: operators with a TF32X3 (tensor-core) far field are "
+        set_error("htlr_matvec_noalloc: operators with a BF16X6 (tensor-core) far field are "
                   "not supported; use htlr_matvec");
         return HTLR_EUNSUPPORTED;
     }

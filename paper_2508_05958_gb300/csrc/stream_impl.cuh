@@ -216,9 +216,9 @@ static void launch_stream_policy(const StreamArgs &a)
 {
     const int ntasks = a.t1 - a.t0;
     if (ntasks <= 0) return;
-    const int threads = 256, wpb = threads / 32;
+    const int threads = a.threads == 128 ? 128 : 256, wpb = threads / 32;
     int blocks = (ntasks + wpb - 1) / wpb;
-    const int cap = 152 * 8;
+    const int cap = 152 * (a.ctas_per_sm > 0 ? a.ctas_per_sm : 8);
     if (blocks > cap) blocks = cap;
     size_t smem = sizeof(typename P::XT) * (size_t)wpb * a.max_cols * a.nrhs;
 #define HTLR_NR_CASE(R)                                                          \

@@ -25,7 +25,11 @@ NUM_STAGES = 4
 SYMBOLS = ("htlr_construct", "htlr_construct_ex", "htlr_matvec", "htlr_matvec_timed",
            "htlr_matvec_host", "htlr_matvec_noalloc", "htlr_gmres", "htlr_free",
            "htlr_info", "htlr_set_stream", "htlr_sync", "htlr_last_error",
-           "htlr_last_launch_count")
+           "htlr_last_launch_count", "htlr_plan_create", "htlr_plan_launch",
+           "htlr_plan_launches", "htlr_plan_free", "htlr_autotune", "htlr_autotune_clear_cache",
+           "htlr_server_create", "htlr_server_add_operator", "htlr_server_submit",
+           "htlr_server_poll", "htlr_server_wait", "htlr_server_get_stats",
+           "htlr_server_destroy")
 
 
 class HTLRError(RuntimeError):
@@ -71,6 +75,49 @@ class htlr_gmres_result(ctypes.Structure):
                 ("refinements", ctypes.c_int), ("rel_residual", ctypes.c_double),
                 ("converged", ctypes.c_int)]
 
+
+class htlr_tune_result(ctypes.Structure):
+    _fields_ = [("task_bytes", ctypes.c_size_t), ("stream_ctas_per_sm", ctypes.c_int),
+                ("stream_threads", ctypes.c_int), ("tc_stages", ctypes.c_int),
+                ("ms", ctypes.c_float), ("default_ms", ctypes.c_float),
+                ("candidates", ctypes.c_int), ("from_cache", ctypes.c_int)]
+
+
+class htlr_server_options(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_size_t), ("max_active", ctypes.c_int),
+                ("max_batch", ctypes.c_int), ("mixed", ctypes.c_int),
+                ("inner_precision", ctypes.c_int), ("restart", ctypes.c_int),
+                ("tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
+                ("max_iters", ctypes.c_int), ("use_graphs", ctypes.c_int),
+                ("autotune_ms", ctypes.c_double)]
+
+
+class htlr_operator_spec(ctypes.Structure):
+    _fields_ = [("kernel_type", ctypes.c_int), ("kscale", ctypes.c_double),
+                ("kparam", ctypes.c_double), ("d", ctypes.c_int), ("n", ctypes.c_int),
+                ("leaf", ctypes.c_int), ("r", ctypes.c_int), ("eta", ctypes.c_double),
+                ("a", ctypes.POINTER(ctypes.c_double)), ("storage", ctypes.c_int)]
+
+
+class htlr_request_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("error", ctypes.c_int), ("iterations", ctypes.c_int),
+                ("matvecs", ctypes.c_int), ("refinements", ctypes.c_int),
+                ("rel_residual", ctypes.c_double), ("converged", ctypes.c_int),
+                ("submit_s", ctypes.c_double), ("admit_s", ctypes.c_double),
+                ("done_s", ctypes.c_double)]
+
+
+class htlr_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong),
+                ("failed", ctypes.c_longlong), ("active", ctypes.c_int), ("pending", ctypes.c_int),
+                ("steps", ctypes.c_longlong), ("batched_matvecs", ctypes.c_longlong),
+                ("matvec_columns", ctypes.c_longlong), ("max_batch_seen", ctypes.c_int),
+                ("constructions", ctypes.c_longlong), ("evictions", ctypes.c_longlong),
+                ("bytes_in_use", ctypes.c_longlong), ("bytes_peak", ctypes.c_longlong),
+                ("bytes_budget", ctypes.c_longlong), ("resident_operators", ctypes.c_int)]
+
+
+REQ_QUEUED, REQ_ACTIVE, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
 
 _lock = threading.Lock()
 _lib = None
@@ -127,6 +174,34 @@ def load(build_if_missing: bool = True):
         L.htlr_last_error.restype = ctypes.c_char_p
         L.htlr_last_launch_count.argtypes = [vp]
         L.htlr_last_launch_count.restype = ctypes.c_int
+        L.htlr_plan_create.argtypes = [vp, vp, vp, ctypes.c_int, P(vp)]
+        L.htlr_plan_create.restype = ctypes.c_int
+        L.htlr_plan_launch.argtypes = [vp]
+        L.htlr_plan_launch.restype = ctypes.c_int
+        L.htlr_plan_launches.argtypes = [vp]
+        L.htlr_plan_launches.restype = ctypes.c_int
+        L.htlr_plan_free.argtypes = [vp]
+        L.htlr_plan_free.restype = None
+        L.htlr_autotune.argtypes = [vp, ctypes.c_int, ctypes.c_double, P(htlr_tune_result)]
+        L.htlr_autotune.restype = ctypes.c_int
+        L.htlr_autotune_clear_cache.argtypes = []
+        L.htlr_autotune_clear_cache.restype = None
+        L.htlr_server_create.argtypes = [P(htlr_server_options), P(vp)]
+        L.htlr_server_create.restype = ctypes.c_int
+        L.htlr_server_add_operator.argtypes = [vp, P(htlr_operator_spec), P(ctypes.c_int)]
+        L.htlr_server_add_operator.restype = ctypes.c_int
+        L.htlr_server_submit.argtypes = [vp, ctypes.c_int, P(ctypes.c_double), P(ctypes.c_double),
+                                         P(ctypes.c_longlong)]
+        L.htlr_server_submit.restype = ctypes.c_int
+        L.htlr_server_poll.argtypes = [vp, ctypes.c_longlong, P(htlr_request_info)]
+        L.htlr_server_poll.restype = ctypes.c_int
+        L.htlr_server_wait.argtypes = [vp, ctypes.c_longlong, ctypes.c_double,
+                                       P(htlr_request_info)]
+        L.htlr_server_wait.restype = ctypes.c_int
+        L.htlr_server_get_stats.argtypes = [vp, P(htlr_server_stats)]
+        L.htlr_server_get_stats.restype = ctypes.c_int
+        L.htlr_server_destroy.argtypes = [vp]
+        L.htlr_server_destroy.restype = None
         _lib = L
         return L
 
@@ -289,3 +364,106 @@ class Operator:
             self.close()
         except Exception:
             pass
+
+
+def htlr_plan_create(H, u, f, nrhs=None):
+    """Capture f = A u (fixed device buffers) into a CUDA graph; returns the plan (int)."""
+    if nrhs is None:
+        nrhs = 1 if u.dim() == 1 else u.shape[0]
+    P = ctypes.c_void_p()
+    _check(load().htlr_plan_create(H, _dptr(u), _dptr(f), nrhs, ctypes.byref(P)))
+    return P.value
+
+
+def htlr_plan_launch(P):
+    _check(load().htlr_plan_launch(P))
+
+
+def htlr_plan_launches(P) -> int:
+    return load().htlr_plan_launches(P)
+
+
+def htlr_plan_free(P):
+    load().htlr_plan_free(P)
+
+
+def htlr_autotune(H, nrhs=1, budget_ms=2000.0) -> dict:
+    """Time launch-shape candidates for nrhs right-hand sides and apply the fastest."""
+    r = htlr_tune_result()
+    _check(load().htlr_autotune(H, nrhs, float(budget_ms), ctypes.byref(r)))
+    return {k: getattr(r, k) for k, _ in htlr_tune_result._fields_}
+
+
+def htlr_autotune_clear_cache():
+    load().htlr_autotune_clear_cache()
+
+
+def _struct_dict(x):
+    return {k: getattr(x, k) for k, _ in x._fields_}
+
+
+def server_options(**kw) -> htlr_server_options:
+    """Options with the library's defaults (see htlr_server_create) overridden by kw."""
+    o = htlr_server_options(0, 64, 16, 1, PREC_FP32, 30, 1e-10, 1e-4, 3000, 1, 0.0)
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Server:
+    """Continuous-batching solve server (htlr_server_*): submit(op, f) -> request id,
+    wait(id) -> (u, info).  Host numpy arrays in and out."""
+
+    def __init__(self, **options):
+        self._L = load()
+        self._o = server_options(**options)
+        h = ctypes.c_void_p()
+        _check(self._L.htlr_server_create(ctypes.byref(self._o), ctypes.byref(h)))
+        self._h = h.value
+        self._keep = {}      # request id -> output array (must outlive the request)
+        self._N = {}
+
+    def add_operator(self, ktype, d, n, leaf, r, eta, *, kscale=1.0, kparam=0.0, a=None,
+                     storage=STORE_AUTO) -> int:
+        a = None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+        spec = htlr_operator_spec(ktype, kscale, kparam, d, n, leaf, r, eta, _hptr(a), storage)
+        op = ctypes.c_int()
+        _check(self._L.htlr_server_add_operator(self._h, ctypes.byref(spec), ctypes.byref(op)))
+        self._N[op.value] = n ** d
+        return op.value
+
+    def submit(self, op, f) -> int:
+        f = np.ascontiguousarray(f, dtype=np.float64).reshape(-1)
+        if op in self._N and f.size != self._N[op]:
+            raise ValueError("f must hold N values")
+        u = np.zeros_like(f)
+        rid = ctypes.c_longlong()
+        _check(self._L.htlr_server_submit(self._h, op, _hptr(f), _hptr(u), ctypes.byref(rid)))
+        self._keep[rid.value] = u
+        return rid.value
+
+    def poll(self, rid) -> dict:
+        info = htlr_request_info()
+        _check(self._L.htlr_server_poll(self._h, rid, ctypes.byref(info)))
+        return _struct_dict(info)
+
+    def wait(self, rid, timeout_s=-1.0):
+        info = htlr_request_info()
+        _check(self._L.htlr_server_wait(self._h, rid, float(timeout_s), ctypes.byref(info)))
+        return self._keep.pop(rid), _struct_dict(info)
+
+    def stats(self) -> dict:
+        st = htlr_server_stats()
+        _check(self._L.htlr_server_get_stats(self._h, ctypes.byref(st)))
+        return _struct_dict(st)
+
+    def close(self):
+        if self._h:
+            self._L.htlr_server_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
