@@ -266,12 +266,13 @@ def tc_tensor_flops(info, w, nrhs):
     return total * -(-nrhs // 64)
 
 
-def stream_roofline(info, w, nrhs, stream_ms, hbm_peak, hbm_src, bf16_peak=None):
+def stream_roofline(info, w, nrhs, stream_ms, hbm_peak, hbm_src, bf16_peak=None,
+                    executed_flops=None):
     fp, np_ = info["far_precision"], info["near_precision"]
     if fp == 3:
         far, near, far_u, near_u = stream_elements(info, w)
         t = stream_ms * 1e-3
-        executed = tc_tensor_flops(info, w, nrhs)
+        executed = executed_flops if executed_flops else tc_tensor_flops(info, w, nrhs)
         peak = bf16_peak or 1895.3
         useful = 2.0 * (far + (near if np_ == 3 else 0.0)) * nrhs
         held = far_u * PREC_BYTES[fp] + (near_u * PREC_BYTES[np_] if info["storage"] != 3 else 0)
@@ -279,7 +280,9 @@ def stream_roofline(info, w, nrhs, stream_ms, hbm_peak, hbm_src, bf16_peak=None)
                 "algorithmic_bytes_per_launch": held, "hbm_achieved_gbs": held / t / 1e9,
                 "unit": "TFLOP/s", "frac": executed / t / 1e12 / peak,
                 "peak_source": "measured bf16 (MEASURED_PEAKS.json, burst)",
-                "kernel": "tc_stream_kernel (tcgen05 kind::f16, BF16x6)", "kernel_ms": stream_ms,
+                "kernel": ("tc_group_kernel" if info.get("tc_grouped") else "tc_stream_kernel")
+                          + " (tcgen05 kind::f16, BF16x6; stage time includes operand packing)",
+                "kernel_ms": stream_ms,
                 "executed_tensor_flops_per_launch": executed,
                 "useful_fp32_equivalent_tflops": useful / t / 1e12, "traffic": None,
                 "precision": {"far": PREC_NAME[fp], "near": PREC_NAME[np_]}}
@@ -430,7 +433,7 @@ def run_gpu(args, w):
         import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
-    step_ms, stage = [], np.zeros(4)
+    step_ms, stage = [], np.zeros(5)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     for k in range(args.steps):
@@ -456,7 +459,7 @@ def run_gpu(args, w):
 
     # roofline of the dominant kernel (the block stream)
     roof = stream_roofline(info, w, nrhs, stage_ms[1], hbm_peak, hbm_src,
-                           peaks.get("bf16_tflops"))
+                           peaks.get("bf16_tflops"), htlr.htlr_tensor_flops(H, nrhs))
 
     # end to end through the host-buffer entry point (pinned host memory, copies timed)
     uh = torch.from_numpy(np.ascontiguousarray(U.T)).pin_memory().numpy()
@@ -479,7 +482,8 @@ def run_gpu(args, w):
                    "(256 MB write); block bytes held: %.3f GB" % (roof["algorithmic_bytes_per_launch"] / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "construct_s": construct_s, "stage_ms": {"up": stage_ms[0],
-                   "stream": stage_ms[1], "reduce": stage_ms[2], "out": stage_ms[3]},
+                   "stream": stage_ms[1], "near_generated": stage_ms[2],
+                   "reduce": stage_ms[3], "out": stage_ms[4]},
                    "bytes_total": info["bytes_total"], "far_per_level": info["far_per_level"],
                    "near_blocks": info["near_blocks"]},
         "roofline": roof,

@@ -131,6 +131,9 @@ typedef struct {
     size_t bytes_cores, bytes_near, bytes_factors, bytes_work, bytes_total;
     double diag_value;                /* K_ii w_i on the uniform grid (eq. (1.4)) */
     int far_precision, near_precision;  /* htlr_precision in use */
+    int tc_grouped;                   /* BF16X6 block lists on the target-grouped tensor-core
+                                         kernel (SHARED): bit l for far level l, bit 31 for
+                                         the inadmissible leaves */
 } htlr_stats;
 
 typedef struct htlr_handle htlr_handle;
@@ -177,11 +180,12 @@ int htlr_matvec_host(htlr_handle *H, const double *u_host, double *f_host, int n
 /*
  * htlr_matvec_timed -- htlr_matvec that also measures, with CUDA events recorded on the
  * handle's stream, the device time of each stage: stage_ms[0] upward contractions,
- * [1] block streaming (cores and dense blocks), [2] per-row reductions, [3] downward
- * expansion + output.  Times are summed over RHS chunks.  Synchronous (waits for the
- * stream).  stage_ms: host array of HTLR_NUM_STAGES floats.
+ * [1] block streaming (cores and held dense blocks, on CUDA or tensor cores, with the
+ * packing of their operands), [2] the generated near field, [3] per-row reductions,
+ * [4] downward expansion + output.  Times are summed over RHS chunks.  Synchronous
+ * (waits for the stream).  stage_ms: host array of HTLR_NUM_STAGES floats.
  */
-#define HTLR_NUM_STAGES 4
+#define HTLR_NUM_STAGES 5
 int htlr_matvec_timed(const htlr_handle *H, const double *u, double *f, int nrhs,
                       float *stage_ms);
 
@@ -393,6 +397,11 @@ int htlr_sync(const htlr_handle *H);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char *htlr_last_error(void);
+
+/* BF16 tensor-core FLOPs (2 M N K summed over the MMAs, padding and the six split
+ * products included) one htlr_matvec of nrhs right-hand sides executes on H; 0 when H
+ * has no BF16X6 block list.  Host-side count, no device work. */
+double htlr_tensor_flops(const htlr_handle *H, int nrhs);
 
 /* Number of kernel launches the last htlr_matvec on H enqueued. */
 int htlr_last_launch_count(const htlr_handle *H);

@@ -171,6 +171,75 @@ static int tc_stages(const TcShape &t, int Rp)
     return S < 2 ? 2 : S;
 }
 
+// Grouped tensor-core shape of Nd x Kd blocks (see tc_group.cu).
+static TcgShape tcg_shape(int Nd, int Kd)
+{
+    TcgShape t;
+    t.Kd = Kd;
+    t.Nd = Nd;
+    t.nch = (Kd + 15) / 16;
+    t.Npad = (Nd + 15) / 16 * 16;
+    if (t.Npad > 256) t.Npad = (Nd + 31) / 32 * 32;   // two MMAs of Npad / 2 (a multiple of 16)
+    t.nN = t.Npad > 256 ? 2 : 1;
+    t.Nh = t.Npad / t.nN;
+    t.NGb = t.Npad / 8;
+    t.core_elems = (long long)t.nch * 3 * t.NGb * 128;
+    t.box_elems = (long long)3 * t.nch * (kTcRpMax / 8) * 128;
+    return t;
+}
+
+// Class offset lists of one block list (rows = boxes of a level with nb1 per dimension,
+// lexicographic): per parity class of the target box, the union of its rows' offsets
+// sigma - tau with their block ids.  Valid only if every row of a class holds exactly
+// the class offsets whose source lies inside the domain, each with one block id;
+// returns false otherwise (the block list then stays on the per-row kernel).
+static bool build_classes(int d, int nb1, const std::vector<int> &rowptr, const std::vector<int> &col,
+                          const std::vector<int> &blk, std::vector<int4v> &out, int start[8],
+                          int count[8])
+{
+    const long long nbox = d == 3 ? (long long)nb1 * nb1 * nb1 : (long long)nb1 * nb1;
+    std::map<std::tuple<int, int, int>, int> cls[8];
+    auto coords = [&](long long b, int &b1, int &b2, int &b3) {
+        b1 = (int)(b % nb1);
+        b2 = (int)((b / nb1) % nb1);
+        b3 = d == 3 ? (int)(b / ((long long)nb1 * nb1)) : 0;
+    };
+    for (long long t = 0; t < nbox; ++t) {
+        int b1, b2, b3;
+        coords(t, b1, b2, b3);
+        const int c = (b1 & 1) + 2 * (b2 & 1) + 4 * (b3 & 1);
+        for (int e = rowptr[t]; e < rowptr[t + 1]; ++e) {
+            int s1, s2, s3;
+            coords(col[e], s1, s2, s3);
+            auto key = std::make_tuple(s3 - b3, s2 - b2, s1 - b1);
+            auto it = cls[c].find(key);
+            if (it == cls[c].end()) cls[c][key] = blk[e];
+            else if (it->second != blk[e]) return false;
+        }
+    }
+    out.clear();
+    for (int c = 0; c < 8; ++c) {
+        start[c] = (int)out.size();
+        count[c] = (int)cls[c].size();
+        if (count[c] > 1024) return false;
+        for (auto &kv : cls[c])
+            out.push_back(int4v{std::get<2>(kv.first), std::get<1>(kv.first), std::get<0>(kv.first),
+                                kv.second});
+    }
+    for (long long t = 0; t < nbox; ++t) {
+        int b1, b2, b3;
+        coords(t, b1, b2, b3);
+        const int c = (b1 & 1) + 2 * (b2 & 1) + 4 * (b3 & 1);
+        int inside = 0;
+        for (int i = start[c]; i < start[c] + count[c]; ++i) {
+            const int s1 = b1 + out[i].x, s2 = b2 + out[i].y, s3 = b3 + out[i].z;
+            inside += s1 >= 0 && s1 < nb1 && s2 >= 0 && s2 < nb1 && s3 >= 0 && (d == 2 || s3 < nb1);
+        }
+        if (inside != rowptr[t + 1] - rowptr[t]) return false;
+    }
+    return true;
+}
+
 // CUDA-core stream tasks: runs of consecutive entries of one block row holding about
 // `task_bytes` of blocks each (at least one entry), a partial-sum slot of nrc x ld
 // doubles per task, and per row the index of its first task (the reductions sum a row's
@@ -672,10 +741,26 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
                 Lv.d_cores = f32;
             }
             if (H->far_prec == kPrecBF16X6) {
-                // packed split-BF16 chunks for the tensor-core stream
+                // packed split-BF16 chunks for the tensor-core stream: grouped by target
+                // (one block per offset, SHARED) when the level's offsets form classes
+                std::vector<int4v> cl;
+                Lv.tg = tcg_shape(Lv.pd, Lv.pd);
+                Lv.tcg = !stored && Lv.tg.Npad <= 512 &&
+                         build_classes(d, 1 << lv, Lv.far_rowptr, Lv.far_col, Lv.far_core, cl,
+                                       Lv.cls_start, Lv.cls_count);
+                if (Lv.tcg) {
+                    Lv.h_cls = cl;
+                    if (dalloc(H, &Lv.d_cls, cl.size())) return HTLR_ECUDA;
+                    HTLR_CK(cudaMemcpyAsync(Lv.d_cls, cl.data(), sizeof(int4v) * cl.size(),
+                                            cudaMemcpyHostToDevice, s));
+                }
                 uint16_t *pk = nullptr;
-                int rc2 = dalloc(H, &pk, (size_t)Lv.ncores * Lv.tc.blk_elems);
-                if (rc2 == HTLR_OK)
+                int rc2 = dalloc(H, &pk, (size_t)Lv.ncores * (Lv.tcg ? Lv.tg.core_elems
+                                                                     : Lv.tc.blk_elems));
+                if (rc2 == HTLR_OK && Lv.tcg)
+                    launch_tcg_pack_blocks(dcore, Lv.ncores, Lv.ld, Lv.pd, Lv.pd, Lv.tg.nch,
+                                           Lv.tg.NGb, pk, s);
+                else if (rc2 == HTLR_OK)
                     launch_tc_pack_blocks(dcore, Lv.ncores, Lv.ld, Lv.pd, Lv.pd, Lv.tc.mtiles,
                                           Lv.tc.kc, Lv.tc.nchunks, pk, s);
                 cudaError_t e2 = cudaStreamSynchronize(s);
@@ -805,9 +890,24 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
             HTLR_CK(cudaMemcpyAsync(H->d_diagpts, dv.data(), sizeof(double) * N,
                                     cudaMemcpyHostToDevice, s));
             HTLR_CK(cudaStreamSynchronize(s));
+            std::vector<int4v> cl;
+            H->near_tg = tcg_shape(rows_leaf, rows_leaf);
+            H->near_tcg = !stored && H->near_tg.Npad <= 512 &&
+                          build_classes(d, 1 << L, H->near_rowptr, H->near_col, H->near_blk, cl,
+                                        H->near_cls_start, H->near_cls_count);
+            if (H->near_tcg) {
+                H->h_near_cls = cl;
+                if (dalloc(H, &H->d_near_cls, cl.size())) return HTLR_ECUDA;
+                HTLR_CK(cudaMemcpyAsync(H->d_near_cls, cl.data(), sizeof(int4v) * cl.size(),
+                                        cudaMemcpyHostToDevice, s));
+            }
             uint16_t *pk = nullptr;
-            int rc2 = dalloc(H, &pk, (size_t)H->nnear_unique * H->near_tc.blk_elems);
-            if (rc2 == HTLR_OK)
+            int rc2 = dalloc(H, &pk, (size_t)H->nnear_unique * (H->near_tcg ? H->near_tg.core_elems
+                                                                            : H->near_tc.blk_elems));
+            if (rc2 == HTLR_OK && H->near_tcg)
+                launch_tcg_pack_blocks(dnear, H->nnear_unique, H->near_ld, rows_leaf, rows_leaf,
+                                       H->near_tg.nch, H->near_tg.NGb, pk, s);
+            else if (rc2 == HTLR_OK)
                 launch_tc_pack_blocks(dnear, H->nnear_unique, H->near_ld, rows_leaf, rows_leaf,
                                       H->near_tc.mtiles, H->near_tc.kc, H->near_tc.nchunks, pk, s);
             cudaError_t e2 = cudaStreamSynchronize(s);
@@ -888,9 +988,16 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
             Lv.tc_t0 = (int)H->tasks_tc.size();
             row_tasks(lv, Lv.far_rowptr, Lv.nbox, Lv.ld, Lv.row_task_tc);
             Lv.tc_t1 = (int)H->tasks_tc.size();
-            if (dalloc(H, &Lv.d_row_task_tc, Lv.row_task_tc.size()) ||
-                dalloc(H, &Lv.d_Wp, (size_t)Lv.nbox * Lv.tc.x_elems))
+            if (dalloc(H, &Lv.d_row_task_tc, Lv.row_task_tc.size()))
                 return HTLR_ECUDA;
+            if (Lv.tcg) {
+                if (dalloc(H, &Lv.d_Wg, (size_t)Lv.nbox * Lv.tg.box_elems)) return HTLR_ECUDA;
+                for (int k = 0; k < 3; ++k)
+                    if (tcg_encode_source_map(Lv.tmap[k].b, Lv.d_Wg, Lv.tg.nch, 16 << k, 1 << lv, d))
+                        return fail(HTLR_ECUDA, "tensor map encoding failed");
+            } else if (dalloc(H, &Lv.d_Wp, (size_t)Lv.nbox * Lv.tc.x_elems)) {
+                return HTLR_ECUDA;
+            }
             HTLR_CK(cudaMemcpyAsync(Lv.d_row_task_tc, Lv.row_task_tc.data(),
                                     sizeof(int) * Lv.row_task_tc.size(), cudaMemcpyHostToDevice, s));
         }
@@ -898,9 +1005,17 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
             H->near_tc_t0 = (int)H->tasks_tc.size();
             row_tasks(L + 1, H->near_rowptr, 1 << (d * L), H->near_ld, H->near_row_task_tc);
             H->near_tc_t1 = (int)H->tasks_tc.size();
-            if (dalloc(H, &H->d_near_row_task_tc, H->near_row_task_tc.size()) ||
-                dalloc(H, &H->d_Up, (size_t)(1 << (d * L)) * H->near_tc.x_elems))
+            if (dalloc(H, &H->d_near_row_task_tc, H->near_row_task_tc.size())) return HTLR_ECUDA;
+            if (H->near_tcg) {
+                if (dalloc(H, &H->d_Ug, (size_t)(1 << (d * L)) * H->near_tg.box_elems))
+                    return HTLR_ECUDA;
+                for (int k = 0; k < 3; ++k)
+                    if (tcg_encode_source_map(H->near_tmap[k].b, H->d_Ug, H->near_tg.nch, 16 << k,
+                                              1 << L, d))
+                        return fail(HTLR_ECUDA, "tensor map encoding failed");
+            } else if (dalloc(H, &H->d_Up, (size_t)(1 << (d * L)) * H->near_tc.x_elems)) {
                 return HTLR_ECUDA;
+            }
             HTLR_CK(cudaMemcpyAsync(H->d_near_row_task_tc, H->near_row_task_tc.data(),
                                     sizeof(int) * H->near_row_task_tc.size(),
                                     cudaMemcpyHostToDevice, s));
@@ -948,6 +1063,9 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
     st.diag_value = H->diag;
     st.far_precision = H->far_prec;
     st.near_precision = H->near_prec;
+    st.tc_grouped = H->near_tcg ? (int)(1u << 31) : 0;
+    for (int lv = 1; lv <= L; ++lv)
+        if (H->lev[lv].tcg) st.tc_grouped |= 1 << lv;
     return HTLR_OK;
 }
 
@@ -1087,16 +1205,70 @@ int run_chunk(const htlr_handle *H, const KindDesc *d_kinds, double *part,
             a.err = H->d_err;
             launch_tc_stream(a, s);
         };
+        // grouped path: G = 128 / Rpg targets per MMA
+        const int Rpg = nh <= 16 ? 16 : nh <= 32 ? 32 : 64, tmi = Rpg == 16 ? 0 : Rpg == 32 ? 1 : 2;
+        auto tcg_launch = [&](const TcgShape &tg, const int4v *cls, const int *cs, const int *cc,
+                              int lv, const int *row_task, const void *blocks, int ld,
+                              const TmapBytes &tm) {
+            TcgArgs g{};
+            g.offs = reinterpret_cast<const int4 *>(cls);
+            for (int c = 0; c < 8; ++c) {
+                g.cls_start[c] = cs[c];
+                g.cls_count[c] = cc[c];
+            }
+            g.d = d;
+            g.nb1 = 1 << lv;
+            g.G = 128 / Rpg;
+            g.Rp = Rpg;
+            g.nr = nh;
+            g.nq = (g.nb1 / 2 + g.G - 1) / g.G;
+            const long long nb23 = d == 3 ? (long long)g.nb1 * g.nb1 : g.nb1;
+            g.ngroups = nb23 * 2 * g.nq;
+            g.Nd = tg.Nd;
+            g.nch = tg.nch;
+            g.NGb = tg.NGb;
+            g.Nh = tg.Nh;
+            g.nN = tg.nN;
+            g.blocks = static_cast<const uint16_t *>(blocks);
+            g.core_elems = tg.core_elems;
+            g.tasks = H->d_tasks_tc;
+            g.row_task = row_task;
+            g.part = H->d_part_tc;
+            g.ld = ld;
+            int S = (int)((200 * 1024) / tcg_stage_bytes(tg.NGb));
+            if (S > kTcMaxStages) S = kTcMaxStages;
+            if (H->tc_stages_cap >= 2 && S > H->tc_stages_cap) S = H->tc_stages_cap;
+            g.stages = S < 2 ? 2 : S;
+            int cols = 32;
+            while (cols < tg.Npad) cols *= 2;
+            g.tmem_cols = cols;
+            g.err = H->d_err;
+            launch_tc_group(g, tm.b, s);
+        };
         for (int lv = 1; lv <= L; ++lv) {
             const LevelData &Lv = H->lev[lv];
             if (Lv.nfar == 0) continue;
+            if (Lv.tcg) {
+                launch_tcg_pack_x(W[lv], (long long)H->nrc * Lv.pd, Lv.pd, Lv.nbox, nh, Rpg,
+                                  Lv.tg.nch, 0, d, n, H->leaf, L, nullptr, 0, Lv.d_Wg, s);
+                tcg_launch(Lv.tg, Lv.d_cls, Lv.cls_start, Lv.cls_count, lv, Lv.d_row_task_tc,
+                           Lv.d_cores, Lv.ld, Lv.tmap[tmi]);
+                launches += 2;
+                continue;
+            }
             launch_tc_pack_x(W[lv], (long long)H->nrc * Lv.pd, Lv.pd, Lv.nbox, nh, Rp, Lv.tc.kc,
                              Lv.tc.nchunks, 0, d, n, H->leaf, L, nullptr, 0, Lv.d_Wp, s);
             tc_launch(Lv.tc, Lv.tc_t0, Lv.tc_t1, Lv.d_far_col, Lv.d_far_core, Lv.d_cores, Lv.d_Wp,
                       Lv.pd, Lv.ld);
             launches += 2;
         }
-        if (H->near_prec == kPrecBF16X6) {
+        if (H->near_prec == kPrecBF16X6 && H->near_tcg) {
+            launch_tcg_pack_x(nullptr, 0, H->near_rows, 1 << (d * L), nh, Rpg, H->near_tg.nch, 1,
+                              d, n, H->leaf, L, uc, N, H->d_Ug, s);
+            tcg_launch(H->near_tg, H->d_near_cls, H->near_cls_start, H->near_cls_count, L,
+                       H->d_near_row_task_tc, H->d_near, H->near_ld, H->near_tmap[tmi]);
+            launches += 2;
+        } else if (H->near_prec == kPrecBF16X6) {
             launch_tc_pack_x(nullptr, 0, H->near_rows, 1 << (d * L), nh, Rp, H->near_tc.kc,
                              H->near_tc.nchunks, 1, d, n, H->leaf, L, uc, N, H->d_Up, s);
             tc_launch(H->near_tc, H->near_tc_t0, H->near_tc_t1, H->d_near_col, H->d_near_blk,
@@ -1106,6 +1278,8 @@ int run_chunk(const htlr_handle *H, const KindDesc *d_kinds, double *part,
     } else if (!H->tasks.empty()) {
         launches += launch_streams(H, d_kinds, uc, N, nh, part, s);
     }
+    mark(3);
+    mark(4);
     if (H->near_generated) {
         NearGenArgs g{};
         g.k = H->kern;
@@ -1128,8 +1302,8 @@ int run_chunk(const htlr_handle *H, const KindDesc *d_kinds, double *part,
         launch_near_generated(H->near_prec, g, s);
         ++launches;
     }
-    mark(3);
-    mark(4);
+    mark(5);
+    mark(6);
     for (int lv = 1; lv <= L; ++lv) {
         const LevelData &Lv = H->lev[lv];
         if (Lv.nfar == 0) continue;
@@ -1141,8 +1315,8 @@ int run_chunk(const htlr_handle *H, const KindDesc *d_kinds, double *part,
                               Hs[lv], s);
         ++launches;
     }
-    mark(5);
-    mark(6);
+    mark(7);
+    mark(8);
     OutArgs oa{};
     oa.d = d;
     oa.n = n;
@@ -1172,7 +1346,7 @@ int run_chunk(const htlr_handle *H, const KindDesc *d_kinds, double *part,
     oa.ldf = N;
     launch_out(oa, H->max_leaf_rows, s);
     ++launches;
-    mark(7);
+    mark(9);
     if (tev)
         for (int st = 0; st < HTLR_NUM_STAGES; ++st) {
             cudaEventSynchronize(tev->ev[2 * st + 1]);
@@ -1423,6 +1597,50 @@ int htlr_sync(const htlr_handle *H)
         return fail(HTLR_EDEVICE, buf);
     }
     return HTLR_OK;
+}
+
+double htlr_tensor_flops(const htlr_handle *H, int nrhs)
+{
+    if (!is_live(H) || nrhs < 1 || !H->tc) return 0.0;
+    const int d = H->d, L = H->L;
+    double total = 0.0;
+    // grouped kernel: every (group, offset) with a source inside the domain, all chunks
+    auto grouped = [&](const TcgShape &tg, const std::vector<int4v> &cl, const int *cs,
+                       const int *cc, int lv, int Rpg) {
+        const int nb1 = 1 << lv, G = 128 / Rpg, nq = (nb1 / 2 + G - 1) / G;
+        const int nb23 = d == 3 ? nb1 * nb1 : nb1;
+        long long pairs = 0;
+        for (int b23 = 0; b23 < nb23; ++b23)
+            for (int c1 = 0; c1 < 2; ++c1)
+                for (int j = 0; j < nq; ++j) {
+                    const int b2 = b23 % nb1, b3 = d == 3 ? b23 / nb1 : 0, t0 = c1 + 2 * j * G;
+                    const int c = c1 + 2 * (b2 & 1) + 4 * (b3 & 1);
+                    for (int i = cs[c]; i < cs[c] + cc[c]; ++i) {
+                        const int s2 = b2 + cl[i].y, s3 = b3 + cl[i].z, lo = t0 + cl[i].x;
+                        pairs += s2 >= 0 && s2 < nb1 && (d == 2 || (s3 >= 0 && s3 < nb1)) &&
+                                 lo + 2 * (G - 1) >= 0 && lo < nb1;
+                    }
+                }
+        return (double)pairs * tg.nch * 6.0 * 2.0 * 128.0 * tg.Npad * 16.0;
+    };
+    auto per_row = [&](const TcShape &ts, long long nblk, int Rp) {
+        return (double)nblk * ts.nchunks * (ts.kc / 16) * 6.0 * ts.mtiles * 2.0 * 128.0 * Rp * 16.0;
+    };
+    for (int c0 = 0; c0 < nrhs; c0 += H->nrc) {
+        const int nh = std::min(H->nrc, nrhs - c0);
+        const int Rp = (nh + 15) / 16 * 16, Rpg = nh <= 16 ? 16 : nh <= 32 ? 32 : 64;
+        for (int lv = 1; lv <= L; ++lv) {
+            const LevelData &Lv = H->lev[lv];
+            if (Lv.nfar == 0) continue;
+            total += Lv.tcg ? grouped(Lv.tg, Lv.h_cls, Lv.cls_start, Lv.cls_count, lv, Rpg)
+                            : per_row(Lv.tc, Lv.nfar, Rp);
+        }
+        if (H->near_prec == kPrecBF16X6)
+            total += H->near_tcg ? grouped(H->near_tg, H->h_near_cls, H->near_cls_start,
+                                           H->near_cls_count, L, Rpg)
+                                 : per_row(H->near_tc, H->nnear, Rp);
+    }
+    return total;
 }
 
 int htlr_last_launch_count(const htlr_handle *H)

@@ -69,12 +69,27 @@ struct KindDesc {
     long long x_box_stride;  // doubles per box in x (nrc * pd)
 };
 
-// Shape of a block list in the packed split-TF32 layout of the tensor-core stream.
+// Shape of a block list in the packed split-BF16 layout of the tensor-core stream.
 constexpr int kTcRpMax = 64;  // right-hand sides per tensor-core pass
 struct TcShape {
     int rows = 0, cols = 0, mtiles = 0, kc = 0, nchunks = 0;
     long long blk_elems = 0;     // bf16 elements per packed block
     long long x_elems = 0;       // bf16 elements per packed source box (for kTcRpMax)
+};
+
+// Grouped tensor-core form of a SHARED block list (tc_group.cu): blocks Nd x Kd packed
+// as [chunk of 16 columns][split][row group][kcore][8][8], sources per box as
+// [split][chunk][row group][kcore][8][8]; the MMA's N (block rows) in nN pieces of Nh.
+struct TcgShape {
+    int Kd = 0, Nd = 0, nch = 0, Npad = 0, NGb = 0, Nh = 0, nN = 0;
+    long long core_elems = 0;    // bf16 elements per packed block
+    long long box_elems = 0;     // bf16 elements per packed source box at 64 RHS
+};
+struct alignas(64) TmapBytes {   // an encoded CUtensorMap (128 bytes)
+    unsigned char b[128];
+};
+struct int4v {                    // (o1, o2, o3, block id) of a class offset list
+    int x, y, z, w;
 };
 
 struct LevelData {
@@ -101,6 +116,15 @@ struct LevelData {
     int task0 = 0, task1 = 0;               // task range (far) of this level
     std::vector<int> row_task_begin;        // per tau: first task; size nbox + 1
     int *d_row_task = nullptr;
+    // grouped tensor-core path (SHARED storage): class offset lists, packed sources,
+    // tensor maps of the sources for 16, 32 and 64 right-hand sides
+    int tcg = 0;
+    TcgShape tg;
+    int cls_start[8] = {0}, cls_count[8] = {0};
+    int4v *d_cls = nullptr;
+    std::vector<int4v> h_cls;
+    uint16_t *d_Wg = nullptr;
+    TmapBytes tmap[3];
 };
 
 struct Plan;  // forward
@@ -151,6 +175,13 @@ struct htlr_handle {
     htlr::TcShape near_tc;
     uint16_t *d_Up = nullptr;        // packed u per leaf
     int near_tc_t0 = 0, near_tc_t1 = 0;
+    int near_tcg = 0;                // grouped tensor-core path for the near field
+    htlr::TcgShape near_tg;
+    int near_cls_start[8] = {0}, near_cls_count[8] = {0};
+    htlr::int4v *d_near_cls = nullptr;
+    std::vector<htlr::int4v> h_near_cls;
+    uint16_t *d_Ug = nullptr;
+    htlr::TmapBytes near_tmap[3];
     std::vector<int> near_row_task_tc;
     int *d_near_row_task_tc = nullptr;
     int *d_err = nullptr;
@@ -295,6 +326,32 @@ struct NearGenArgs {
     int max_rows;
 };
 void launch_near_generated(int prec, const NearGenArgs &a, cudaStream_t s);
+// ---- tc_group.cu: grouped tensor-core stream for SHARED block lists ----
+struct TcgArgs {
+    const int4 *offs;                  // class offset lists (o1, o2, o3, block id)
+    int cls_start[8], cls_count[8];
+    int d, nb1;                        // dimension, boxes per dimension at this level
+    int G, Rp, nr;                     // targets per group (G Rp = 128), padded / real RHS
+    int nq;                            // groups along one parity line of dimension 1
+    long long ngroups;
+    int Nd, nch, NGb, Nh, nN;
+    const uint16_t *blocks;
+    long long core_elems;
+    const Task *tasks;
+    const int *row_task;
+    double *part;
+    int ld;
+    int stages, tmem_cols;
+    int *err;
+};
+void launch_tcg_pack_blocks(const double *src, long long nblk, int ld, int Nd, int Kd, int nch,
+                            int NGb, uint16_t *dst, cudaStream_t s);
+void launch_tcg_pack_x(const double *W, long long w_box_stride, int Kd, int nbox, int nr, int Rp,
+                       int nch, int is_near, int d, int n, int leaf, int L, const double *u,
+                       long long ldu, uint16_t *dst, cudaStream_t s);
+size_t tcg_stage_bytes(int NGb);
+void launch_tc_group(const TcgArgs &a, const void *tmap, cudaStream_t s);
+int tcg_encode_source_map(void *tmap_out, const uint16_t *base, int nch, int Rp, int nb1, int d);
 // ---- tc_stream.cu: tensor-core (tcgen05) block stream for many right-hand sides ----
 constexpr int kTcMaxStages = 8;
 struct TcArgs {

@@ -62,109 +62,210 @@ __device__ __forceinline__ float kernel_value<float>(const KernelDesc &k, int d,
     }
 }
 
-constexpr int kGenPer = 4;  // target rows per thread: leaves of up to 1024 points
+// One CTA per target leaf; thread t owns the target rows t, t + T, ..., t + (PER-1) T
+// (T threads).  The source points of one near leaf at a time are staged in shared memory
+// as (y relative to the target leaf's corner, w_j u_j for every RHS, contiguous), and
+// every thread sweeps them with its PER rows held in registers, so one staged point
+// feeds PER kernel evaluations and PER x NR multiply-adds.  The kernel type is resolved
+// once per launch (a template argument of the sweep), not per pair.  All small per-
+// dimension arrays are indexed with compile-time indices so they stay in registers.
+struct KParams {
+    double scale, param, inv2s2;  // inv2s2 = 1 / (2 sigma^2) for the Gaussian
+    int deg;
+};
 
-template <typename T, int NR>
+template <typename T, int KT>
+__device__ __forceinline__ T kv_eval(const KParams &k, int d, T r2, T dx0, T dx1, T dx2)
+{
+    if constexpr (KT == HTLR_K_LOG) {
+        return (T)k.scale * (T)0.5 * log(r2);
+    } else if constexpr (KT == HTLR_K_INV_R) {
+        if constexpr (sizeof(T) == 4) return (T)k.scale * rsqrtf(r2);
+        else return k.scale / sqrt(r2);
+    } else if constexpr (KT == HTLR_K_EXP_R) {
+        if constexpr (sizeof(T) == 4) return (T)k.scale * expf(-(r2 * rsqrtf(r2)));
+        else return k.scale * exp(-sqrt(r2));
+    } else if constexpr (KT == HTLR_K_GAUSS) {
+        return (T)k.scale * exp(-r2 * (T)k.inv2s2);
+    } else if constexpr (KT == HTLR_K_POLY) {
+        const T dxs[3] = {dx0, dx1, dx2};
+        T v = (T)k.scale;
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+            if (l < d) {
+                const T b = dxs[l] + (T)2 + (T)0.5 * (T)l;
+                T pw = (T)1;
+                for (int e = 0; e < k.deg; ++e) pw *= b;
+                v *= pw;
+            }
+        }
+        return v;
+    } else {
+        return (T)k.scale;
+    }
+}
+
+template <typename T, int NR, int PER, int KT>
+__device__ __forceinline__ void sweep(const KParams &k, int d, int cols, bool self,
+                                      const T *__restrict__ sy, const T *__restrict__ swu,
+                                      const T (&xr)[PER][3], const int (&irow)[PER],
+                                      T (&acc)[PER][NR])
+{
+    for (int j = 0; j < cols; ++j) {
+        const T y0 = sy[4 * j], y1 = sy[4 * j + 1], y2 = sy[4 * j + 2];
+        T wu[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) wu[r] = swu[j * NR + r];
+#pragma unroll
+        for (int m = 0; m < PER; ++m) {
+            const T dx0 = xr[m][0] - y0, dx1 = xr[m][1] - y1, dx2 = xr[m][2] - y2;
+            const T r2 = dx0 * dx0 + dx1 * dx1 + dx2 * dx2;
+            T kv = kv_eval<T, KT>(k, d, r2, dx0, dx1, dx2);
+            kv = (self && j == irow[m]) ? (T)0 : kv;   // the diagonal is added separately
+#pragma unroll
+            for (int r = 0; r < NR; ++r) acc[m][r] += kv * wu[r];
+        }
+    }
+}
+
+// box of leaf index g: first grid line and point count per dimension (unused dims: 0, 1)
+__device__ __forceinline__ void leaf_box(const LevelGeom &lg, int d, int L, int g, int (&f)[3],
+                                         int (&c)[3])
+{
+    const int m1 = (1 << L) - 1;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        f[k] = 0;
+        c[k] = 1;
+        if (k < d) {
+            const int bk = (g >> (L * k)) & m1;
+            f[k] = lg.first[k][bk];
+            c[k] = lg.cnt[k][bk];
+        }
+    }
+}
+
+template <typename T, int NR, int PER>
 __global__ void __launch_bounds__(256) near_gen_kernel(NearGenArgs A, int r0, int nr)
 {
     extern __shared__ __align__(16) unsigned char sm_raw[];
     const int tau = blockIdx.x, d = A.d, n = A.n, L = A.L;
-    const int m1 = (1 << L) - 1;
-    int tf[3] = {0, 0, 0}, tc[3] = {1, 1, 1};
-    double lo[3] = {0.0, 0.0, 0.0};
-    for (int k = 0; k < d; ++k) {
-        int tk = (tau >> (L * k)) & m1;
-        tf[k] = A.leafg.first[k][tk];
-        tc[k] = A.leafg.cnt[k][tk];
-        lo[k] = ldexp((double)tk, -L);
-    }
+    int tf[3], tc[3];
+    leaf_box(A.leafg, d, L, tau, tf, tc);
+    double lo[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) lo[k] = k < d ? ldexp((double)((tau >> (L * k)) & ((1 << L) - 1)), -L) : 0.0;
     const int rows = tc[0] * tc[1] * tc[2];
-    // shared: source coordinates (d x max_rows, T), w u (NR x max_rows, T)
+    KParams kp;
+    kp.scale = A.k.scale;
+    kp.param = A.k.param;
+    kp.inv2s2 = A.k.type == HTLR_K_GAUSS ? 1.0 / (2.0 * A.k.param * A.k.param) : 0.0;
+    kp.deg = (int)A.k.param;
+    // shared: source points (4 per point: y_1..y_3, pad), w u (max_rows x NR)
     T *sy = reinterpret_cast<T *>(sm_raw);
-    T *swu = sy + 3 * A.max_rows;
-    // own target rows
-    T xr[kGenPer][3];
-    long long nat[kGenPer];
-    T acc[kGenPer][NR];
-    for (int m = 0; m < kGenPer; ++m) {
+    T *swu = sy + 4 * A.max_rows;
+    T xr[PER][3];
+    int irow[PER];
+    long long nat[PER];
+    T acc[PER][NR];
+#pragma unroll
+    for (int m = 0; m < PER; ++m) {
         const int i = threadIdx.x + blockDim.x * m;
+        irow[m] = i;
         nat[m] = -1;
+#pragma unroll
         for (int r = 0; r < NR; ++r) acc[m][r] = (T)0;
-        for (int k = 0; k < 3; ++k) xr[m][k] = (T)0;
+        // rows past the leaf evaluate a far-away dummy point (finite, never written)
+        xr[m][0] = xr[m][1] = xr[m][2] = (T)4;
         if (i < rows) {
-            int j1 = i % tc[0], j23 = i / tc[0], j2 = j23 % tc[1], j3 = j23 / tc[1];
-            int gi[3] = {tf[0] + j1, tf[1] + j2, tf[2] + j3};
+            const int j1 = i % tc[0], j23 = i / tc[0], j2 = j23 % tc[1], j3 = j23 / tc[1];
+            const int gi[3] = {tf[0] + j1, tf[1] + j2, tf[2] + j3};
             long long na = 0, str = 1;
-            for (int k = 0; k < d; ++k) {
-                xr[m][k] = (T)(A.coords[(long long)k * n + gi[k]] - lo[k]);
-                na += (long long)gi[k] * str;
-                str *= n;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                xr[m][k] = (T)0;
+                if (k < d) {
+                    xr[m][k] = (T)(A.coords[(long long)k * n + gi[k]] - lo[k]);
+                    na += (long long)gi[k] * str;
+                    str *= n;
+                }
             }
             nat[m] = na;
         }
     }
     for (int e = A.rowptr[tau]; e < A.rowptr[tau + 1]; ++e) {
         const int sg = A.col[e];
-        int sf[3] = {0, 0, 0}, sc[3] = {1, 1, 1};
-        for (int k = 0; k < d; ++k) {
-            int sk = (sg >> (L * k)) & m1;
-            sf[k] = A.leafg.first[k][sk];
-            sc[k] = A.leafg.cnt[k][sk];
-        }
+        int sf[3], sc[3];
+        leaf_box(A.leafg, d, L, sg, sf, sc);
         const int cols = sc[0] * sc[1] * sc[2];
         __syncthreads();
         for (int j = threadIdx.x; j < cols; j += blockDim.x) {
-            int j1 = j % sc[0], j23 = j / sc[0], j2 = j23 % sc[1], j3 = j23 / sc[1];
-            int gj[3] = {sf[0] + j1, sf[1] + j2, sf[2] + j3};
+            const int j1 = j % sc[0], j23 = j / sc[0], j2 = j23 % sc[1], j3 = j23 / sc[1];
+            const int gj[3] = {sf[0] + j1, sf[1] + j2, sf[2] + j3};
             long long na = 0, str = 1;
             double w = 1.0;
-            for (int k = 0; k < d; ++k) {
-                sy[k * A.max_rows + j] = (T)(A.coords[(long long)k * n + gj[k]] - lo[k]);
-                w *= A.width[(long long)k * n + gj[k]];
-                na += (long long)gj[k] * str;
-                str *= n;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                T y = (T)0;
+                if (k < d) {
+                    y = (T)(A.coords[(long long)k * n + gj[k]] - lo[k]);
+                    w *= A.width[(long long)k * n + gj[k]];
+                    na += (long long)gj[k] * str;
+                    str *= n;
+                }
+                sy[4 * j + k] = y;
             }
-            for (int r = 0; r < nr; ++r)
-                swu[r * A.max_rows + j] = (T)(w * A.u[na + A.ldu * (r0 + r)]);
+            sy[4 * j + 3] = (T)0;
+#pragma unroll
+            for (int r = 0; r < NR; ++r)
+                swu[j * NR + r] = r < nr ? (T)(w * A.u[na + A.ldu * (r0 + r)]) : (T)0;
         }
         __syncthreads();
         const bool self = (sg == tau);
-        for (int m = 0; m < kGenPer; ++m) {
-            const int i = threadIdx.x + blockDim.x * m;
-            if (i >= rows) continue;
-            for (int j = 0; j < cols; ++j) {
-                if (self && j == i) continue;
-                T dx[3];
-                T r2 = (T)0;
-                for (int k = 0; k < d; ++k) {
-                    dx[k] = xr[m][k] - sy[k * A.max_rows + j];
-                    r2 += dx[k] * dx[k];
-                }
-                const T kv = kernel_value<T>(A.k, d, r2, dx);
-#pragma unroll
-                for (int r = 0; r < NR; ++r)
-                    if (r < nr) acc[m][r] += kv * swu[r * A.max_rows + j];
-            }
+        switch (A.k.type) {
+        case HTLR_K_LOG: sweep<T, NR, PER, HTLR_K_LOG>(kp, d, cols, self, sy, swu, xr, irow, acc); break;
+        case HTLR_K_INV_R: sweep<T, NR, PER, HTLR_K_INV_R>(kp, d, cols, self, sy, swu, xr, irow, acc); break;
+        case HTLR_K_EXP_R: sweep<T, NR, PER, HTLR_K_EXP_R>(kp, d, cols, self, sy, swu, xr, irow, acc); break;
+        case HTLR_K_GAUSS: sweep<T, NR, PER, HTLR_K_GAUSS>(kp, d, cols, self, sy, swu, xr, irow, acc); break;
+        case HTLR_K_POLY: sweep<T, NR, PER, HTLR_K_POLY>(kp, d, cols, self, sy, swu, xr, irow, acc); break;
+        default: sweep<T, NR, PER, HTLR_K_CONST>(kp, d, cols, self, sy, swu, xr, irow, acc); break;
         }
     }
-    for (int m = 0; m < kGenPer; ++m) {
+#pragma unroll
+    for (int m = 0; m < PER; ++m) {
         if (nat[m] < 0) continue;
         const double dg = A.diag[nat[m]] + (A.a ? A.a[nat[m]] : 0.0);
-        for (int r = 0; r < nr; ++r) {
-            const double uv = A.u[nat[m] + A.ldu * (r0 + r)];
-            A.f[nat[m] + A.ldf * (r0 + r)] = (double)acc[m][r] + dg * uv;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            if (r < nr) {
+                const double uv = A.u[nat[m] + A.ldu * (r0 + r)];
+                A.f[nat[m] + A.ldf * (r0 + r)] = (double)acc[m][r] + dg * uv;
+            }
         }
     }
 }
 
-template <typename T, int NR>
-static void launch_gen_t(const NearGenArgs &a, int r0, int nr, cudaStream_t s)
+template <typename T, int NR, int PER>
+static void launch_gen_t(const NearGenArgs &a, int r0, int nr, int threads, cudaStream_t s)
 {
-    size_t smem = sizeof(T) * (size_t)a.max_rows * (3 + NR);
+    size_t smem = sizeof(T) * (size_t)a.max_rows * (4 + NR);
     if (smem > 48 * 1024)
-        cudaFuncSetAttribute(near_gen_kernel<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-    near_gen_kernel<T, NR><<<1 << (a.d * a.L), 256, smem, s>>>(a, r0, nr);
+        cudaFuncSetAttribute(near_gen_kernel<T, NR, PER>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    near_gen_kernel<T, NR, PER><<<1 << (a.d * a.L), threads, smem, s>>>(a, r0, nr);
+}
+
+template <typename T, int NR>
+static void launch_gen_nr(const NearGenArgs &a, int r0, int nr, cudaStream_t s)
+{
+    // the fewest rows per thread that cover the largest leaf with at most 256 threads
+    int per = 2;
+    while (per < 4 && (a.max_rows + per - 1) / per > 256) ++per;
+    int threads = ((a.max_rows + per - 1) / per + 31) / 32 * 32;
+    if (threads < 32) threads = 32;
+    if (per == 2) launch_gen_t<T, NR, 2>(a, r0, nr, threads, s);
+    else if (per == 3) launch_gen_t<T, NR, 3>(a, r0, nr, threads, s);
+    else launch_gen_t<T, NR, 4>(a, r0, nr, threads, s);
 }
 
 template <typename T>
@@ -172,11 +273,9 @@ static void launch_gen_prec(const NearGenArgs &a, cudaStream_t s)
 {
     for (int r0 = 0; r0 < a.nrhs; r0 += 16) {
         int nr = a.nrhs - r0 < 16 ? a.nrhs - r0 : 16;
-        if (nr <= 1) launch_gen_t<T, 1>(a, r0, nr, s);
-        else if (nr <= 2) launch_gen_t<T, 2>(a, r0, nr, s);
-        else if (nr <= 4) launch_gen_t<T, 4>(a, r0, nr, s);
-        else if (nr <= 8) launch_gen_t<T, 8>(a, r0, nr, s);
-        else launch_gen_t<T, 16>(a, r0, nr, s);
+        if (nr <= 1) launch_gen_nr<T, 1>(a, r0, nr, s);
+        else if (nr <= 4) launch_gen_nr<T, 4>(a, r0, nr, s);
+        else launch_gen_nr<T, 16>(a, r0, nr, s);
     }
 }
 

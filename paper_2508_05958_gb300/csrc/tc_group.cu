@@ -1,0 +1,384 @@
+// Tensor-core block stream for SHARED operators, grouped by target (tcgen05, sm_103a).
+//
+// With SHARED storage every admissible block of a level with the same box offset
+// o = sigma - tau is the same matrix B_o (and likewise for the inadmissible leaves), so
+// the products B_o X_{tau+o} of several targets tau can read B_o once.  Per level, the
+// targets of one parity class (b_1 mod 2, b_2 mod 2, b_3 mod 2) have the same offsets,
+// except where tau + o leaves the domain.  A group is G same-parity targets along
+// dimension 1, tau_k = tau_0 + 2k e_1, and the kernel forms the transposed products
+//
+//     Y^T[(k, r), t] += sum_s X_{tau_k + o}[s, r] B_o[t, s]      (every offset o),
+//
+// an MMA with M = G x Rp = 128 rows (target, right-hand side), N = the block's rows and
+// K = its columns, FP32 accumulation in TMEM.  One CTA owns a group for all of its
+// offsets, so Y_tau is complete when it is written: no partial sums across CTAs.
+//
+// Operands (three-way BF16 split, the six products a_i b_j with i + j <= 2):
+//   A = the source tensors X_{tau_k + o} of the G targets: one 5-D TMA tensor load per
+//       split gathers them, because the sources of a group sit at stride 2 boxes along
+//       dimension 1 (the tensor is the packed source array viewed as
+//       [b_23][q][c_1][split, chunk, row group][128 elements], b_1 = 2q + c_1); sources
+//       outside the domain read zeros;
+//   B = B_o, packed at construction chunk by chunk, one bulk copy per stage.
+// Both in the canonical K-major layout without swizzle: 8-row groups 256 bytes apart
+// (SBO), the two 8-column core matrices of a 16-column chunk 128 bytes apart (LBO).
+//
+// One elected thread issues the copies and the MMAs (S-stage ring, "full" and "empty"
+// mbarriers); after a group, the four warps read the accumulator with tcgen05.ld and
+// write the group's rows as FP64 partials.  Every wait is bounded: on timeout the kernel
+// records kDevTimeout, drains what it issued and frees TMEM.
+#include <cuda.h>
+
+#include "tc_common.cuh"
+
+namespace htlr {
+
+using namespace tcc;
+
+namespace {
+
+constexpr int kGThreads = 128;
+constexpr int kMaxGroupOffsets = 1024;
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------
+// Construction: pack FP64 blocks ([s][t], leading dimension ld, Nd x Kd) into
+// [chunk][split][row group (NGb)][kcore (2)][8][8] split-BF16 elements.
+// ---------------------------------------------------------------------------------
+__global__ void tcg_pack_blocks_kernel(const double *__restrict__ src, long long nblk, int ld,
+                                       int Nd, int Kd, int nch, int NGb, uint16_t *__restrict__ dst)
+{
+    const long long per_chunk = (long long)kSplits * NGb * 128;
+    const long long per_blk = per_chunk * nch;
+    const long long total = per_blk * nblk;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long b = idx / per_blk;
+        long long rem = idx % per_blk;
+        const int ch = (int)(rem / per_chunk);
+        rem %= per_chunk;
+        const int split = (int)(rem / (NGb * 128));
+        rem %= NGb * 128;
+        const int gn = (int)(rem / 128), o = (int)(rem % 128);
+        const int c = o / 64, row = (o % 64) / 8, e = o % 8;
+        const int t = gn * 8 + row, s = ch * 16 + c * 8 + e;
+        const double x =
+            (t < Nd && s < Kd) ? src[b * (long long)ld * Kd + (long long)s * ld + t] : 0.0;
+        dst[idx] = bf16_split(x, split);
+    }
+}
+
+void launch_tcg_pack_blocks(const double *src, long long nblk, int ld, int Nd, int Kd, int nch,
+                            int NGb, uint16_t *dst, cudaStream_t s)
+{
+    if (nblk > 0)
+        tcg_pack_blocks_kernel<<<152 * 8, 256, 0, s>>>(src, nblk, ld, Nd, Kd, nch, NGb, dst);
+}
+
+// ---------------------------------------------------------------------------------
+// Per matvec: pack the source operand per box as [split][chunk][row group (Rp / 8)]
+// [kcore (2)][8][8]: far field W [box][r][pd] (FP64), near field u gathered per leaf.
+// Rows r >= nr and columns s >= Kd are zero.
+// ---------------------------------------------------------------------------------
+__global__ void tcg_pack_x_kernel(const double *__restrict__ W, long long w_box_stride, int Kd,
+                                  int nbox, int nr, int Rp, int nch, int is_near, int d, int n,
+                                  int leaf, int L, const double *__restrict__ u, long long ldu,
+                                  uint16_t *__restrict__ dst)
+{
+    const int NGa = Rp / 8;
+    const long long per_split = (long long)nch * NGa * 128;
+    const long long per_box = kSplits * per_split;
+    const long long total = per_box * nbox;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long box = idx / per_box;
+        long long rem = idx % per_box;
+        const int split = (int)(rem / per_split);
+        rem %= per_split;
+        const int ch = (int)(rem / (NGa * 128));
+        rem %= NGa * 128;
+        const int g = (int)(rem / 128), o = (int)(rem % 128);
+        const int c = o / 64, row = (o % 64) / 8, e = o % 8;
+        const int r = g * 8 + row, s = ch * 16 + c * 8 + e;
+        double x = 0.0;
+        if (r < nr && s < Kd) {
+            if (is_near) {
+                const int nl1 = 1 << L;
+                long long nat = 0, str = 1;
+                int ss = s;
+                for (int k = 0; k < d; ++k) {
+                    const int bk = (int)((box >> (L * k)) & (nl1 - 1));
+                    nat += (long long)(bk * leaf + ss % leaf) * str;
+                    ss /= leaf;
+                    str *= n;
+                }
+                x = u[nat + ldu * r];
+            } else {
+                x = W[box * w_box_stride + (long long)r * Kd + s];
+            }
+        }
+        dst[idx] = bf16_split(x, split);
+    }
+}
+
+void launch_tcg_pack_x(const double *W, long long w_box_stride, int Kd, int nbox, int nr, int Rp,
+                       int nch, int is_near, int d, int n, int leaf, int L, const double *u,
+                       long long ldu, uint16_t *dst, cudaStream_t s)
+{
+    tcg_pack_x_kernel<<<152 * 8, 256, 0, s>>>(W, w_box_stride, Kd, nbox, nr, Rp, nch, is_near, d,
+                                              n, leaf, L, u, ldu, dst);
+}
+
+// ---------------------------------------------------------------------------------
+// The grouped stream.
+// ---------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kGThreads, 1)
+    tc_group_kernel(const __grid_constant__ CUtensorMap tmap, TcgArgs A)
+{
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ uint64_t full_bar[kTcMaxStages], empty_bar[kTcMaxStages], done_bar;
+    __shared__ uint32_t tmem_holder;
+    __shared__ int abort_flag, n_valid;
+    __shared__ short valid_idx[kMaxGroupOffsets];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int S = A.stages, G = A.G, Rp = A.Rp, NGa = Rp / 8, nch = A.nch, NGb = A.NGb;
+    const uint32_t a_split_bytes = 128u * 16u * 2u;             // 128 rows x 16 columns
+    const uint32_t a_bytes = kSplits * a_split_bytes;
+    const uint32_t b_split_bytes = (uint32_t)NGb * 256u;        // Npad rows x 16 columns
+    const uint32_t b_bytes = kSplits * b_split_bytes;
+    const uint32_t stage_bytes = a_bytes + b_bytes;
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+        }
+        mbar_init(&done_bar, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_holder)),
+                     "r"(A.tmem_cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_holder;
+    // D f32, A and B bf16, both K-major, N = Nh, M = 128
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(A.Nh >> 3) << 17) |
+                           ((uint32_t)(128 >> 4) << 24);
+    const uint32_t lbo = 128, sbo = 256;
+    const int pa[6] = {0, 0, 1, 0, 1, 2}, pb[6] = {0, 1, 0, 2, 1, 0};
+    const int nb1 = A.nb1;
+    uint32_t full_ph = 0, empty_ph = 0, pending = 0, done_ph = 0;
+    bool ok = true;
+
+    for (long long grp = blockIdx.x; grp < A.ngroups && ok; grp += gridDim.x) {
+        // group -> (b23, c1, j): tau_0 = (c1 + 2 j G, b2, b3)
+        const int j = (int)(grp % A.nq);
+        const long long rest = grp / A.nq;
+        const int c1 = (int)(rest % 2);
+        const int b23 = (int)(rest / 2);
+        const int b2 = b23 % nb1, b3 = A.d == 3 ? b23 / nb1 : 0;
+        const int t0b1 = c1 + 2 * j * G;
+        const int cls = c1 + 2 * (b2 & 1) + 4 * (b3 & 1);
+        const int4 *offs = A.offs + A.cls_start[cls];
+        const int noff = A.cls_count[cls];
+        // offsets with at least one source inside the domain (warp 0, in list order)
+        if (warp == 0) {
+            int cnt = 0;
+            for (int base = 0; base < noff; base += 32) {
+                const int i = base + lane;
+                bool v = false;
+                if (i < noff) {
+                    const int4 o = offs[i];
+                    const int s2 = b2 + o.y, s3 = b3 + o.z, lo = t0b1 + o.x;
+                    v = s2 >= 0 && s2 < nb1 && (A.d == 2 || (s3 >= 0 && s3 < nb1)) &&
+                        lo + 2 * (G - 1) >= 0 && lo < nb1;
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, v);
+                if (v) valid_idx[cnt + __popc(m & ((1u << lane) - 1u))] = (short)i;
+                cnt += __popc(m);
+            }
+            if (lane == 0) n_valid = cnt;
+        }
+        __syncthreads();
+        const long long total = (long long)n_valid * nch;
+        if (tid == 0 && total > 0) {
+            auto load = [&](long long q) -> bool {
+                const int s = (int)(q % S);
+                if (pending & (1u << s)) {
+                    if (!mbar_wait(&empty_bar[s], (empty_ph >> s) & 1)) return false;
+                    empty_ph ^= 1u << s;
+                    pending &= ~(1u << s);
+                }
+                const int4 o = offs[valid_idx[(int)(q / nch)]];
+                const int ch = (int)(q % nch);
+                const int s0 = t0b1 + o.x;                 // b_1 of the first source
+                const int sc1 = s0 & 1;                    // (two's complement: also < 0)
+                const int sq0 = (s0 - sc1) / 2;
+                const int sb23 = (b2 + o.y) + nb1 * (b3 + o.z);
+                unsigned char *st = sm + (size_t)s * stage_bytes;
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                                 smem_u32(&full_bar[s])),
+                             "r"(stage_bytes)
+                             : "memory");
+                for (int a = 0; a < kSplits; ++a)
+                    tensor_load_5d(st + a * a_split_bytes, &tmap, 0, (a * nch + ch) * NGa, sc1,
+                                   sq0, sb23, &full_bar[s]);
+                const uint16_t *gb = A.blocks + (long long)o.w * A.core_elems +
+                                     (long long)ch * (b_bytes / 2);
+                bulk_load(st + a_bytes, gb, b_bytes, &full_bar[s]);
+                return true;
+            };
+            for (long long q = 0; q < total && q < S && ok; ++q) ok = load(q);
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            for (long long q = 0; q < total && ok; ++q) {
+                const int s = (int)(q % S);
+                if (!mbar_wait(&full_bar[s], (full_ph >> s) & 1)) {
+                    ok = false;
+                    break;
+                }
+                full_ph ^= 1u << s;
+                const uint32_t a_base = smem_u32(sm + (size_t)s * stage_bytes);
+                const uint32_t b_base = a_base + a_bytes;
+                for (int pr = 0; pr < 6; ++pr) {
+                    const uint64_t ad = smem_desc(a_base + pa[pr] * a_split_bytes, lbo, sbo);
+                    for (int h = 0; h < A.nN; ++h) {
+                        const uint32_t b_addr =
+                            b_base + pb[pr] * b_split_bytes + (uint32_t)h * (uint32_t)(A.Nh / 8) * 256u;
+                        const uint32_t accumulate = (q == 0 && pr == 0) ? 0u : 1u;
+                        mma_bf16(tmem + (uint32_t)(h * A.Nh), ad, smem_desc(b_addr, lbo, sbo),
+                                 idesc, accumulate);
+                    }
+                }
+                mma_commit(&empty_bar[s]);
+                pending |= 1u << s;
+                if (q >= 1 && q - 1 + S < total) ok = load(q - 1 + S);
+            }
+            mma_commit(&done_bar);
+        }
+        __syncthreads();
+        if (tid == 0 && !ok) abort_flag = 1;
+        __syncthreads();
+        if (abort_flag) {
+            ok = false;
+            break;
+        }
+        // accumulator row m = k Rp + r: target tau_k = tau_0 + 2k e_1, right-hand side r
+        const int m = warp * 32 + lane, k = m / Rp, r = m % Rp;
+        const int tb1 = t0b1 + 2 * k;
+        double *out = nullptr;
+        if (tb1 < nb1 && r < A.nr) {
+            const int tau = tb1 + nb1 * b23;
+            const int ta = A.row_task[tau];
+            if (A.row_task[tau + 1] > ta) out = A.part + A.tasks[ta].part + (long long)r * A.ld;
+        }
+        if (total == 0) {
+            if (out)
+                for (int t = 0; t < A.Nd; ++t) out[t] = 0.0;
+            continue;
+        }
+        const int late = __syncthreads_or(mbar_wait(&done_bar, done_ph) ? 0 : 1);
+        if (late) {
+            if (tid == 0) atomicExch(A.err, (int)kDevTimeout);
+            ok = false;
+        }
+        done_ph ^= 1;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (ok) {
+            for (int c0 = 0; c0 < A.nN * A.Nh; c0 += 8) {
+                uint32_t v[8];
+                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                      "=r"(v[6]), "=r"(v[7])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
+                if (out)
+                    for (int jj = 0; jj < 8; ++jj)
+                        if (c0 + jj < A.Nd) out[c0 + jj] = (double)__uint_as_float(v[jj]);
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;");
+    }
+    if (!ok) {
+        if (tid == 0) {
+            atomicExch(A.err, (int)kDevTimeout);
+            mma_commit(&done_bar);
+            mbar_wait(&done_bar, done_ph);
+            for (int s = 0; s < S; ++s)
+                if (pending & (1u << s)) mbar_wait(&empty_bar[s], (empty_ph >> s) & 1);
+        }
+        __syncthreads();
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(A.tmem_cols));
+}
+
+size_t tcg_stage_bytes(int NGb) { return (size_t)kSplits * 128 * 16 * 2 + (size_t)kSplits * NGb * 256; }
+
+void launch_tc_group(const TcgArgs &a, const void *tmap, cudaStream_t s)
+{
+    if (a.ngroups <= 0) return;
+    const size_t smem = tcg_stage_bytes(a.NGb) * a.stages;
+    cudaFuncSetAttribute(tc_group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int grid = a.ngroups < 152 ? (int)a.ngroups : 152;
+    tc_group_kernel<<<grid, kGThreads, smem, s>>>(*static_cast<const CUtensorMap *>(tmap), a);
+}
+
+// ---------------------------------------------------------------------------------
+// Host: the tensor map of a packed source array for Rp right-hand sides at a level with
+// nb1 boxes per dimension: [b23][q][c1][split, chunk, row group][128 elements].
+// ---------------------------------------------------------------------------------
+namespace {
+using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                              const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                              const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                              CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeFn encode_fn()
+{
+    static EncodeFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeFn>(p);
+    }
+    return fn;
+}
+}  // namespace
+
+int tcg_encode_source_map(void *tmap_out, const uint16_t *base, int nch, int Rp, int nb1, int d)
+{
+    EncodeFn fn = encode_fn();
+    if (!fn) return HTLR_ECUDA;
+    const int NGa = Rp / 8;
+    const int G = 128 / Rp;
+    const cuuint64_t box_elems = (cuuint64_t)kSplits * nch * NGa * 128;
+    const cuuint64_t nb23 = d == 3 ? (cuuint64_t)nb1 * nb1 : (cuuint64_t)nb1;
+    cuuint64_t dims[5] = {128, (cuuint64_t)kSplits * nch * NGa, 2, (cuuint64_t)(nb1 / 2), nb23};
+    cuuint64_t strides[4] = {256, box_elems * 2, box_elems * 4, box_elems * 2 * nb1};
+    cuuint32_t box[5] = {128, (cuuint32_t)NGa, 1, (cuuint32_t)G, 1};
+    cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    CUresult r = fn(static_cast<CUtensorMap *>(tmap_out), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5,
+                    const_cast<uint16_t *>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? HTLR_OK : HTLR_ECUDA;
+}
+
+}  // namespace htlr

@@ -21,7 +21,7 @@ STORE_AUTO, STORE_STORED, STORE_SHARED = 0, 1, 2
 PREC_FP64, PREC_DF64, PREC_FP32, PREC_BF16X6 = 0, 1, 2, 3
 MAX_LEVELS = 16
 
-NUM_STAGES = 4
+NUM_STAGES = 5
 SYMBOLS = ("htlr_construct", "htlr_construct_ex", "htlr_matvec", "htlr_matvec_timed",
            "htlr_matvec_host", "htlr_matvec_noalloc", "htlr_gmres", "htlr_free",
            "htlr_info", "htlr_set_stream", "htlr_sync", "htlr_last_error",
@@ -29,7 +29,7 @@ SYMBOLS = ("htlr_construct", "htlr_construct_ex", "htlr_matvec", "htlr_matvec_ti
            "htlr_plan_launches", "htlr_plan_free", "htlr_autotune", "htlr_autotune_clear_cache",
            "htlr_server_create", "htlr_server_add_operator", "htlr_server_submit",
            "htlr_server_poll", "htlr_server_wait", "htlr_server_get_stats",
-           "htlr_server_destroy")
+           "htlr_server_destroy", "htlr_tensor_flops")
 
 
 class HTLRError(RuntimeError):
@@ -62,7 +62,7 @@ class htlr_stats(ctypes.Structure):
                 ("bytes_near", ctypes.c_size_t), ("bytes_factors", ctypes.c_size_t),
                 ("bytes_work", ctypes.c_size_t), ("bytes_total", ctypes.c_size_t),
                 ("diag_value", ctypes.c_double), ("far_precision", ctypes.c_int),
-                ("near_precision", ctypes.c_int)]
+                ("near_precision", ctypes.c_int), ("tc_grouped", ctypes.c_int)]
 
 
 class htlr_gmres_options(ctypes.Structure):
@@ -186,6 +186,8 @@ def load(build_if_missing: bool = True):
         L.htlr_autotune.restype = ctypes.c_int
         L.htlr_autotune_clear_cache.argtypes = []
         L.htlr_autotune_clear_cache.restype = None
+        L.htlr_tensor_flops.argtypes = [vp, ctypes.c_int]
+        L.htlr_tensor_flops.restype = ctypes.c_double
         L.htlr_server_create.argtypes = [P(htlr_server_options), P(vp)]
         L.htlr_server_create.restype = ctypes.c_int
         L.htlr_server_add_operator.argtypes = [vp, P(htlr_operator_spec), P(ctypes.c_int)]
@@ -467,3 +469,8 @@ class Server:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def htlr_tensor_flops(H, nrhs) -> float:
+    """Tensor-core FLOPs one matvec of nrhs right-hand sides executes (0 without BF16X6)."""
+    return load().htlr_tensor_flops(H, nrhs)

@@ -262,6 +262,23 @@ def test_tensor_grid_matches_oracle_htlr(oracle, ktype):
     assert rel(f32, ref) < FP32_TOL
 
 
+@pytest.mark.parametrize("nrhs", [1, 3, 9])
+def test_tensor_grid_large_leaves_generated_near(oracle, nrhs):
+    """Leaves of 7-9 points per dimension (up to 729 rows: three target rows per thread
+    in the generated near field) at every RHS count class of that kernel."""
+    from paper_2508_05958_gb300.workloads import Workload
+    w = Workload("tl", d=3, n=32, ktype=2, leaf=8, p=5, eta=1.0, seed=34)
+    grid = _qgrid(3, 32, seed=9)
+    u = w.u(nrhs=nrhs)
+    f, info = _gpu_tensor(w, grid, u)
+    assert info["storage"] == 3
+    H = oracle.HTLR(3, 32, 2, 8, 5, 1.0, grid=grid, orth=False)
+    ref = H.matvec(u)
+    assert rel(f, ref) < TOL
+    f32, _ = _gpu_tensor(w, grid, u, far_precision=2, near_precision=2)
+    assert rel(f32, ref) < FP32_TOL
+
+
 @pytest.mark.parametrize("near", [0, 2])
 def test_uniform_generated_near_field(oracle, near):
     from paper_2508_05958_gb300.workloads import workload
@@ -300,9 +317,38 @@ def test_tensor_core_stream_matches_oracle(oracle, nrhs):
     u = w.u(nrhs=nrhs)
     f, info = gpu_matvec(w, u, storage=2, far_precision=3, near_precision=3)
     assert info["far_precision"] == 3
+    # SHARED: every far level and the leaves on the target-grouped kernel
+    want = sum(1 << lv for lv, c in enumerate(info["far_per_level"]) if c) - (1 << 31)
+    assert info["tc_grouped"] == want
     ref, _ = _oracle_htlr(oracle, w, u)
     err = rel(f, ref)
     assert err < TC_TOL, err
+
+
+@pytest.mark.parametrize("nrhs", [8, 64])
+def test_tensor_core_stored_blocks_match_oracle(oracle, nrhs):
+    """STORED blocks (one per block, no sharing): the per-row tensor-core kernel."""
+    from paper_2508_05958_gb300.workloads import workload
+    w = workload("c2", n=16)
+    u = w.u(nrhs=nrhs)
+    f, info = gpu_matvec(w, u, storage=1, far_precision=3, near_precision=3)
+    assert info["storage"] == 1 and info["tc_grouped"] == 0
+    ref, _ = _oracle_htlr(oracle, w, u)
+    assert rel(f, ref) < TC_TOL
+
+
+def test_tensor_core_grouped_equals_per_row(oracle):
+    """The grouped and the per-row kernels apply the same split products; per RHS they
+    differ only in the FP32 accumulation order."""
+    from paper_2508_05958_gb300.workloads import workload
+    w = workload("c2", n=16)
+    u = w.u(nrhs=16)
+    fg, ig = gpu_matvec(w, u, storage=2, far_precision=3, near_precision=3)
+    fs, is_ = gpu_matvec(w, u, storage=1, far_precision=3, near_precision=3)
+    assert ig["tc_grouped"] != 0 and is_["tc_grouped"] == 0
+    ref, _ = _oracle_htlr(oracle, w, u)
+    assert rel(fg, ref) < TC_TOL and rel(fs, ref) < TC_TOL
+    assert rel(fg, fs) < TC_TOL
 
 
 @pytest.mark.parametrize("case", [dict(name="c1", over={}), dict(name="c3", over=dict(n=32)),
