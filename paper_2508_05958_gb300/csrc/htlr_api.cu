@@ -240,6 +240,39 @@ static bool build_classes(int d, int nb1, const std::vector<int> &rowptr, const 
     return true;
 }
 
+// Offsets of a class list with at least one source inside the domain for the group
+// (b23, c1, j) of G targets (the work of that group in the grouped kernel).
+static long long group_valid(int d, int nb1, int G, int b23, int c1, int j,
+                             const std::vector<int4v> &cl, const int *cs, const int *cc)
+{
+    const int b2 = b23 % nb1, b3 = d == 3 ? b23 / nb1 : 0, t0 = c1 + 2 * j * G;
+    const int c = c1 + 2 * (b2 & 1) + 4 * (b3 & 1);
+    long long v = 0;
+    for (int i = cs[c]; i < cs[c] + cc[c]; ++i) {
+        const int s2 = b2 + cl[i].y, s3 = b3 + cl[i].z, lo = t0 + cl[i].x;
+        v += s2 >= 0 && s2 < nb1 && (d == 2 || (s3 >= 0 && s3 < nb1)) && lo + 2 * (G - 1) >= 0 &&
+             lo < nb1;
+    }
+    return v;
+}
+
+// Groups of a level for Rp right-hand sides, heaviest first (ties in index order).
+static std::vector<int> group_order(int d, int lv, int Rp, const std::vector<int4v> &cl,
+                                    const int *cs, const int *cc)
+{
+    const int nb1 = 1 << lv, G = 128 / Rp, nq = (nb1 / 2 + G - 1) / G;
+    const int nb23 = d == 3 ? nb1 * nb1 : nb1;
+    std::vector<long long> w((size_t)nb23 * 2 * nq);
+    for (int b23 = 0; b23 < nb23; ++b23)
+        for (int c1 = 0; c1 < 2; ++c1)
+            for (int j = 0; j < nq; ++j)
+                w[((size_t)b23 * 2 + c1) * nq + j] = group_valid(d, nb1, G, b23, c1, j, cl, cs, cc);
+    std::vector<int> ord(w.size());
+    for (size_t i = 0; i < ord.size(); ++i) ord[i] = (int)i;
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return w[a] > w[b]; });
+    return ord;
+}
+
 // CUDA-core stream tasks: runs of consecutive entries of one block row holding about
 // `task_bytes` of blocks each (at least one entry), a partial-sum slot of nrc x ld
 // doubles per task, and per row the index of its first task (the reductions sum a row's
@@ -992,9 +1025,16 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
                 return HTLR_ECUDA;
             if (Lv.tcg) {
                 if (dalloc(H, &Lv.d_Wg, (size_t)Lv.nbox * Lv.tg.box_elems)) return HTLR_ECUDA;
-                for (int k = 0; k < 3; ++k)
+                for (int k = 0; k < 3; ++k) {
                     if (tcg_encode_source_map(Lv.tmap[k].b, Lv.d_Wg, Lv.tg.nch, 16 << k, 1 << lv, d))
                         return fail(HTLR_ECUDA, "tensor map encoding failed");
+                    std::vector<int> ord =
+                        group_order(d, lv, 16 << k, Lv.h_cls, Lv.cls_start, Lv.cls_count);
+                    if (dalloc(H, &Lv.d_order[k], ord.size())) return HTLR_ECUDA;
+                    HTLR_CK(cudaMemcpyAsync(Lv.d_order[k], ord.data(), sizeof(int) * ord.size(),
+                                            cudaMemcpyHostToDevice, s));
+                    HTLR_CK(cudaStreamSynchronize(s));
+                }
             } else if (dalloc(H, &Lv.d_Wp, (size_t)Lv.nbox * Lv.tc.x_elems)) {
                 return HTLR_ECUDA;
             }
@@ -1009,10 +1049,17 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
             if (H->near_tcg) {
                 if (dalloc(H, &H->d_Ug, (size_t)(1 << (d * L)) * H->near_tg.box_elems))
                     return HTLR_ECUDA;
-                for (int k = 0; k < 3; ++k)
+                for (int k = 0; k < 3; ++k) {
                     if (tcg_encode_source_map(H->near_tmap[k].b, H->d_Ug, H->near_tg.nch, 16 << k,
                                               1 << L, d))
                         return fail(HTLR_ECUDA, "tensor map encoding failed");
+                    std::vector<int> ord = group_order(d, L, 16 << k, H->h_near_cls,
+                                                       H->near_cls_start, H->near_cls_count);
+                    if (dalloc(H, &H->d_near_order[k], ord.size())) return HTLR_ECUDA;
+                    HTLR_CK(cudaMemcpyAsync(H->d_near_order[k], ord.data(), sizeof(int) * ord.size(),
+                                            cudaMemcpyHostToDevice, s));
+                    HTLR_CK(cudaStreamSynchronize(s));
+                }
             } else if (dalloc(H, &H->d_Up, (size_t)(1 << (d * L)) * H->near_tc.x_elems)) {
                 return HTLR_ECUDA;
             }
@@ -1020,7 +1067,8 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
                                     sizeof(int) * H->near_row_task_tc.size(),
                                     cudaMemcpyHostToDevice, s));
         }
-        if (dalloc(H, &H->d_tasks_tc, H->tasks_tc.size()) || dalloc(H, &H->d_part_tc, (size_t)ptc))
+        if (dalloc(H, &H->d_tasks_tc, H->tasks_tc.size()) || dalloc(H, &H->d_part_tc, (size_t)ptc) ||
+            dalloc(H, &H->d_grp_counter, (size_t)L + 2))
             return HTLR_ECUDA;
         HTLR_CK(cudaMemcpyAsync(H->d_tasks_tc, H->tasks_tc.data(), sizeof(Task) * H->tasks_tc.size(),
                                 cudaMemcpyHostToDevice, s));
@@ -1209,8 +1257,10 @@ int run_chunk(const htlr_handle *H, const KindDesc *d_kinds, double *part,
         const int Rpg = nh <= 16 ? 16 : nh <= 32 ? 32 : 64, tmi = Rpg == 16 ? 0 : Rpg == 32 ? 1 : 2;
         auto tcg_launch = [&](const TcgShape &tg, const int4v *cls, const int *cs, const int *cc,
                               int lv, const int *row_task, const void *blocks, int ld,
-                              const TmapBytes &tm) {
+                              const TmapBytes &tm, int *counter, const int *order) {
             TcgArgs g{};
+            g.counter = counter;
+            g.order = order;
             g.offs = reinterpret_cast<const int4 *>(cls);
             for (int c = 0; c < 8; ++c) {
                 g.cls_start[c] = cs[c];
@@ -1252,7 +1302,7 @@ int run_chunk(const htlr_handle *H, const KindDesc *d_kinds, double *part,
                 launch_tcg_pack_x(W[lv], (long long)H->nrc * Lv.pd, Lv.pd, Lv.nbox, nh, Rpg,
                                   Lv.tg.nch, 0, d, n, H->leaf, L, nullptr, 0, Lv.d_Wg, s);
                 tcg_launch(Lv.tg, Lv.d_cls, Lv.cls_start, Lv.cls_count, lv, Lv.d_row_task_tc,
-                           Lv.d_cores, Lv.ld, Lv.tmap[tmi]);
+                           Lv.d_cores, Lv.ld, Lv.tmap[tmi], H->d_grp_counter + lv, Lv.d_order[tmi]);
                 launches += 2;
                 continue;
             }
@@ -1266,7 +1316,8 @@ int run_chunk(const htlr_handle *H, const KindDesc *d_kinds, double *part,
             launch_tcg_pack_x(nullptr, 0, H->near_rows, 1 << (d * L), nh, Rpg, H->near_tg.nch, 1,
                               d, n, H->leaf, L, uc, N, H->d_Ug, s);
             tcg_launch(H->near_tg, H->d_near_cls, H->near_cls_start, H->near_cls_count, L,
-                       H->d_near_row_task_tc, H->d_near, H->near_ld, H->near_tmap[tmi]);
+                       H->d_near_row_task_tc, H->d_near, H->near_ld, H->near_tmap[tmi],
+                       H->d_grp_counter + L + 1, H->d_near_order[tmi]);
             launches += 2;
         } else if (H->near_prec == kPrecBF16X6) {
             launch_tc_pack_x(nullptr, 0, H->near_rows, 1 << (d * L), nh, Rp, H->near_tc.kc,
@@ -1612,15 +1663,7 @@ double htlr_tensor_flops(const htlr_handle *H, int nrhs)
         long long pairs = 0;
         for (int b23 = 0; b23 < nb23; ++b23)
             for (int c1 = 0; c1 < 2; ++c1)
-                for (int j = 0; j < nq; ++j) {
-                    const int b2 = b23 % nb1, b3 = d == 3 ? b23 / nb1 : 0, t0 = c1 + 2 * j * G;
-                    const int c = c1 + 2 * (b2 & 1) + 4 * (b3 & 1);
-                    for (int i = cs[c]; i < cs[c] + cc[c]; ++i) {
-                        const int s2 = b2 + cl[i].y, s3 = b3 + cl[i].z, lo = t0 + cl[i].x;
-                        pairs += s2 >= 0 && s2 < nb1 && (d == 2 || (s3 >= 0 && s3 < nb1)) &&
-                                 lo + 2 * (G - 1) >= 0 && lo < nb1;
-                    }
-                }
+                for (int j = 0; j < nq; ++j) pairs += group_valid(d, nb1, G, b23, c1, j, cl, cs, cc);
         return (double)pairs * tg.nch * 6.0 * 2.0 * 128.0 * tg.Npad * 16.0;
     };
     auto per_row = [&](const TcShape &ts, long long nblk, int Rp) {

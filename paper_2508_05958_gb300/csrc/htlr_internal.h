@@ -123,6 +123,7 @@ struct LevelData {
     int cls_start[8] = {0}, cls_count[8] = {0};
     int4v *d_cls = nullptr;
     std::vector<int4v> h_cls;
+    int *d_order[3] = {nullptr, nullptr, nullptr};  // group order for 16, 32, 64 RHS
     uint16_t *d_Wg = nullptr;
     TmapBytes tmap[3];
 };
@@ -180,6 +181,8 @@ struct htlr_handle {
     int near_cls_start[8] = {0}, near_cls_count[8] = {0};
     htlr::int4v *d_near_cls = nullptr;
     std::vector<htlr::int4v> h_near_cls;
+    int *d_near_order[3] = {nullptr, nullptr, nullptr};
+    int *d_grp_counter = nullptr;    // one per level + 1 (grouped tensor-core launches)
     uint16_t *d_Ug = nullptr;
     htlr::TmapBytes near_tmap[3];
     std::vector<int> near_row_task_tc;
@@ -343,6 +346,8 @@ struct TcgArgs {
     int ld;
     int stages, tmem_cols;
     int *err;
+    int *counter;                      // next group (reset to 0 before each launch)
+    const int *order;                  // groups, heaviest first
 };
 void launch_tcg_pack_blocks(const double *src, long long nblk, int ld, int Nd, int Kd, int nch,
                             int NGb, uint16_t *dst, cudaStream_t s);

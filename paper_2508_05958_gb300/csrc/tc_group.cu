@@ -23,10 +23,13 @@
 // Both in the canonical K-major layout without swizzle: 8-row groups 256 bytes apart
 // (SBO), the two 8-column core matrices of a 16-column chunk 128 bytes apart (LBO).
 //
-// One elected thread issues the copies and the MMAs (S-stage ring, "full" and "empty"
-// mbarriers); after a group, the four warps read the accumulator with tcgen05.ld and
-// write the group's rows as FP64 partials.  Every wait is bounded: on timeout the kernel
-// records kDevTimeout, drains what it issued and frees TMEM.
+// Roles: one thread of warp 1 issues the copies into an S-stage ring as soon as a stage
+// is free ("empty" mbarrier, committed by the MMAs that read it); one thread of warp 0
+// waits for each stage ("full" mbarrier, completed by the copies' byte count) and issues
+// its MMAs.  After a group the four warps read the accumulator with tcgen05.ld and write
+// the group's rows as FP64 partials.  Groups are taken heaviest first from an atomic
+// counter over a host-sorted order, so the SMs finish together.  Every wait is bounded:
+// on timeout the kernel records kDevTimeout, drains what it issued and frees TMEM.
 #include <cuda.h>
 
 #include "tc_common.cuh"
@@ -138,8 +141,9 @@ __global__ void __launch_bounds__(kGThreads, 1)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ uint64_t full_bar[kTcMaxStages], empty_bar[kTcMaxStages], done_bar;
-    __shared__ uint32_t tmem_holder;
-    __shared__ int abort_flag, n_valid;
+    __shared__ uint32_t tmem_holder, consumed;
+    __shared__ volatile int abort_flag;
+    __shared__ int n_valid, cur_group;
     __shared__ short valid_idx[kMaxGroupOffsets];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int S = A.stages, G = A.G, Rp = A.Rp, NGa = Rp / 8, nch = A.nch, NGb = A.NGb;
@@ -155,6 +159,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
         }
         mbar_init(&done_bar, 1);
         abort_flag = 0;
+        consumed = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -173,10 +178,20 @@ __global__ void __launch_bounds__(kGThreads, 1)
     const uint32_t lbo = 128, sbo = 256;
     const int pa[6] = {0, 0, 1, 0, 1, 2}, pb[6] = {0, 1, 0, 2, 1, 0};
     const int nb1 = A.nb1;
-    uint32_t full_ph = 0, empty_ph = 0, pending = 0, done_ph = 0;
+    // stage counters run across groups: stage it % S, its use number it / S
+    uint32_t it_p = 0;       // loads issued (producer thread, tid 32)
+    uint32_t it_c = 0;       // stages consumed (MMA thread, tid 0)
+    uint32_t done_ph = 0;
+    int done_pending = 0;    // commits to done_bar not yet waited for (MMA thread)
     bool ok = true;
 
-    for (long long grp = blockIdx.x; grp < A.ngroups && ok; grp += gridDim.x) {
+    while (true) {
+        // next group, heaviest first (dynamic: an atomic counter over a host-sorted order)
+        if (tid == 0) cur_group = atomicAdd(A.counter, 1);
+        __syncthreads();
+        const long long gi = cur_group;
+        if (gi >= A.ngroups) break;
+        const long long grp = A.order[gi];
         // group -> (b23, c1, j): tau_0 = (c1 + 2 j G, b2, b3)
         const int j = (int)(grp % A.nq);
         const long long rest = grp / A.nq;
@@ -207,14 +222,15 @@ __global__ void __launch_bounds__(kGThreads, 1)
         }
         __syncthreads();
         const long long total = (long long)n_valid * nch;
-        if (tid == 0 && total > 0) {
-            auto load = [&](long long q) -> bool {
-                const int s = (int)(q % S);
-                if (pending & (1u << s)) {
-                    if (!mbar_wait(&empty_bar[s], (empty_ph >> s) & 1)) return false;
-                    empty_ph ^= 1u << s;
-                    pending &= ~(1u << s);
+        if (tid == 32 && total > 0) {
+            // producer: refill a stage as soon as the MMAs that read it are done
+            for (long long q = 0; q < total; ++q, ++it_p) {
+                const int s = (int)(it_p % S);
+                if (it_p >= (uint32_t)S && !mbar_wait(&empty_bar[s], ((it_p / S) - 1) & 1)) {
+                    abort_flag = 1;
+                    break;
                 }
+                if (abort_flag) break;
                 const int4 o = offs[valid_idx[(int)(q / nch)]];
                 const int ch = (int)(q % nch);
                 const int s0 = t0b1 + o.x;                 // b_1 of the first source
@@ -232,17 +248,18 @@ __global__ void __launch_bounds__(kGThreads, 1)
                 const uint16_t *gb = A.blocks + (long long)o.w * A.core_elems +
                                      (long long)ch * (b_bytes / 2);
                 bulk_load(st + a_bytes, gb, b_bytes, &full_bar[s]);
-                return true;
-            };
-            for (long long q = 0; q < total && q < S && ok; ++q) ok = load(q);
+            }
+        }
+        if (tid == 0 && total > 0) {
+            // MMA issue: the six split products into every N piece of the accumulator
             asm volatile("tcgen05.fence::after_thread_sync;");
-            for (long long q = 0; q < total && ok; ++q) {
-                const int s = (int)(q % S);
-                if (!mbar_wait(&full_bar[s], (full_ph >> s) & 1)) {
-                    ok = false;
+            for (long long q = 0; q < total; ++q, ++it_c) {
+                const int s = (int)(it_c % S);
+                if (!mbar_wait(&full_bar[s], (it_c / S) & 1)) {
+                    abort_flag = 1;
                     break;
                 }
-                full_ph ^= 1u << s;
+                if (abort_flag) break;
                 const uint32_t a_base = smem_u32(sm + (size_t)s * stage_bytes);
                 const uint32_t b_base = a_base + a_bytes;
                 for (int pr = 0; pr < 6; ++pr) {
@@ -256,13 +273,11 @@ __global__ void __launch_bounds__(kGThreads, 1)
                     }
                 }
                 mma_commit(&empty_bar[s]);
-                pending |= 1u << s;
-                if (q >= 1 && q - 1 + S < total) ok = load(q - 1 + S);
             }
             mma_commit(&done_bar);
+            ++done_pending;
+            consumed = it_c;
         }
-        __syncthreads();
-        if (tid == 0 && !ok) abort_flag = 1;
         __syncthreads();
         if (abort_flag) {
             ok = false;
@@ -283,26 +298,26 @@ __global__ void __launch_bounds__(kGThreads, 1)
             continue;
         }
         const int late = __syncthreads_or(mbar_wait(&done_bar, done_ph) ? 0 : 1);
+        done_ph ^= 1;
+        if (tid == 0) --done_pending;
         if (late) {
             if (tid == 0) atomicExch(A.err, (int)kDevTimeout);
             ok = false;
+            break;
         }
-        done_ph ^= 1;
         asm volatile("tcgen05.fence::after_thread_sync;");
-        if (ok) {
-            for (int c0 = 0; c0 < A.nN * A.Nh; c0 += 8) {
-                uint32_t v[8];
-                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
-                      "=r"(v[6]), "=r"(v[7])
-                    : "r"(taddr));
-                asm volatile("tcgen05.wait::ld.sync.aligned;");
-                if (out)
-                    for (int jj = 0; jj < 8; ++jj)
-                        if (c0 + jj < A.Nd) out[c0 + jj] = (double)__uint_as_float(v[jj]);
-            }
+        for (int c0 = 0; c0 < A.nN * A.Nh; c0 += 8) {
+            uint32_t v[8];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                  "=r"(v[6]), "=r"(v[7])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+            if (out)
+                for (int jj = 0; jj < 8; ++jj)
+                    if (c0 + jj < A.Nd) out[c0 + jj] = (double)__uint_as_float(v[jj]);
         }
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
@@ -311,10 +326,18 @@ __global__ void __launch_bounds__(kGThreads, 1)
     if (!ok) {
         if (tid == 0) {
             atomicExch(A.err, (int)kDevTimeout);
+            // every MMA issued by this CTA finishes before TMEM is released
             mma_commit(&done_bar);
-            mbar_wait(&done_bar, done_ph);
-            for (int s = 0; s < S; ++s)
-                if (pending & (1u << s)) mbar_wait(&empty_bar[s], (empty_ph >> s) & 1);
+            ++done_pending;
+            for (; done_pending > 0; --done_pending) {
+                mbar_wait(&done_bar, done_ph);
+                done_ph ^= 1;
+            }
+        }
+        if (tid == 32) {
+            // every copy issued into shared memory lands before the CTA exits
+            for (uint32_t it = consumed; it < it_p; ++it)
+                mbar_wait(&full_bar[it % S], (it / S) & 1);
         }
         __syncthreads();
     }
@@ -330,6 +353,7 @@ size_t tcg_stage_bytes(int NGb) { return (size_t)kSplits * 128 * 16 * 2 + (size_
 void launch_tc_group(const TcgArgs &a, const void *tmap, cudaStream_t s)
 {
     if (a.ngroups <= 0) return;
+    cudaMemsetAsync(a.counter, 0, sizeof(int), s);
     const size_t smem = tcg_stage_bytes(a.NGb) * a.stages;
     cudaFuncSetAttribute(tc_group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int grid = a.ngroups < 152 ? (int)a.ngroups : 152;
