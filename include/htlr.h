@@ -134,6 +134,7 @@ typedef struct {
     int tc_grouped;                   /* BF16X6 block lists on the target-grouped tensor-core
                                          kernel (SHARED): bit l for far level l, bit 31 for
                                          the inadmissible leaves */
+    int64_t near_point_pairs;         /* sum over inadmissible leaves of |tau| |sigma| */
 } htlr_stats;
 
 typedef struct htlr_handle htlr_handle;
@@ -181,8 +182,9 @@ int htlr_matvec_host(htlr_handle *H, const double *u_host, double *f_host, int n
  * htlr_matvec_timed -- htlr_matvec that also measures, with CUDA events recorded on the
  * handle's stream, the device time of each stage: stage_ms[0] upward contractions,
  * [1] block streaming (cores and held dense blocks, on CUDA or tensor cores, with the
- * packing of their operands), [2] the generated near field, [3] per-row reductions,
- * [4] downward expansion + output.  Times are summed over RHS chunks.  Synchronous
+ * packing of their operands), [2] the near field on the CUDA cores when it is generated
+ * or sits beside a tensor-core far field, [3] per-row reductions, [4] downward
+ * expansion + output.  Times are summed over RHS chunks.  Synchronous
  * (waits for the stream).  stage_ms: host array of HTLR_NUM_STAGES floats.
  */
 #define HTLR_NUM_STAGES 5

@@ -522,14 +522,11 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
         Lv.tc = tc_shape(Lv.pd, Lv.pd);
     }
     H->near_tc = tc_shape(rows_leaf, rows_leaf);
-    // tensor-core stream: both block lists on the tensor cores, or far field on the
-    // tensor cores with a generated near field
+    // tensor-core stream: the far field on the tensor cores, the near field on the tensor
+    // cores too, generated, or held in FP64 / df64 / FP32 for the CUDA-core stream
     if (H->near_prec == kPrecBF16X6 && (H->far_prec != kPrecBF16X6 || H->near_generated))
         return fail(HTLR_EUNSUPPORTED, "a BF16X6 near field needs stored dense blocks and a "
                                        "BF16X6 far field");
-    if (H->far_prec == kPrecBF16X6 && H->near_prec != kPrecBF16X6 && !H->near_generated)
-        return fail(HTLR_EUNSUPPORTED, "a BF16X6 far field needs a BF16X6 or generated near "
-                                       "field");
     H->tc = (H->far_prec == kPrecBF16X6) ? 1 : 0;
 
     // unique offsets (tau - sigma) per level and for the inadmissible leaves
@@ -1101,6 +1098,20 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
     }
     paper += (double)H->nnear * rows_leaf * (double)rows_leaf;
     st.near_blocks = H->nnear;
+    {
+        // point pairs of the near field: sum over inadmissible leaf pairs of |tau| |sigma|
+        const LevelData &Ll = H->lev[L];
+        auto pts = [&](int g) {
+            long long c = 1;
+            for (int k = 0; k < d; ++k) c *= Ll.cnt[k][(g >> (L * k)) & ((1 << L) - 1)];
+            return c;
+        };
+        long long pairs = 0;
+        for (int t = 0; t < (1 << (d * L)); ++t)
+            for (int e = H->near_rowptr[t]; e < H->near_rowptr[t + 1]; ++e)
+                pairs += pts(t) * pts(H->near_col[e]);
+        st.near_point_pairs = pairs;
+    }
     st.unique_near = H->nnear_unique;
     st.paper_storage_doubles = paper;
     st.bytes_cores = sz.cores;
@@ -1331,6 +1342,13 @@ int run_chunk(const htlr_handle *H, const KindDesc *d_kinds, double *part,
     }
     mark(3);
     mark(4);
+    if (H->tc && H->near_prec != kPrecBF16X6 && !H->near_generated && !H->tasks.empty()) {
+        // held near field on the CUDA cores beside a tensor-core far field, four right-hand
+        // sides per pass (its partial-sum slots hold kTcRpMax RHS; pass r0 fills r0 .. r0+3)
+        for (int r0 = 0; r0 < nh; r0 += 4)
+            launches += launch_streams(H, d_kinds, uc + (long long)r0 * N, N, std::min(4, nh - r0),
+                                       part + (long long)r0 * H->near_ld, s);
+    }
     if (H->near_generated) {
         NearGenArgs g{};
         g.k = H->kern;

@@ -62,7 +62,8 @@ class htlr_stats(ctypes.Structure):
                 ("bytes_near", ctypes.c_size_t), ("bytes_factors", ctypes.c_size_t),
                 ("bytes_work", ctypes.c_size_t), ("bytes_total", ctypes.c_size_t),
                 ("diag_value", ctypes.c_double), ("far_precision", ctypes.c_int),
-                ("near_precision", ctypes.c_int), ("tc_grouped", ctypes.c_int)]
+                ("near_precision", ctypes.c_int), ("tc_grouped", ctypes.c_int),
+                ("near_point_pairs", ctypes.c_int64)]
 
 
 class htlr_gmres_options(ctypes.Structure):

@@ -373,11 +373,21 @@ def test_tensor_core_far_with_generated_near(oracle):
     assert rel(f, ref) < TC_TOL
 
 
+@pytest.mark.parametrize("storage,near,nrhs", [(2, 0, 16), (2, 1, 37), (1, 1, 8), (2, 2, 64)])
+def test_tensor_core_far_with_held_cuda_core_near(oracle, storage, near, nrhs):
+    """BF16-split far field on the tensor cores, held near field (FP64, df64 or FP32) on
+    the CUDA cores in passes of four right-hand sides."""
+    from paper_2508_05958_gb300.workloads import workload
+    w = workload("c2", n=16)
+    u = w.u(nrhs=nrhs)
+    f, info = gpu_matvec(w, u, storage=storage, far_precision=3, near_precision=near)
+    assert info["far_precision"] == 3 and info["near_precision"] == near
+    ref, _ = _oracle_htlr(oracle, w, u)
+    assert rel(f, ref) < TC_TOL
+
+
 def test_tensor_core_rejects_unsupported_mixes():
     from paper_2508_05958_gb300 import htlr
-    with pytest.raises(htlr.HTLRError) as ei:
-        htlr.htlr_construct(1, 3, 16, 4, 4, 1.0, storage=2, far_precision=3, near_precision=0)
-    assert ei.value.code == htlr.HTLR_EUNSUPPORTED
     with pytest.raises(htlr.HTLRError) as ei:
         htlr.htlr_construct(1, 3, 16, 4, 4, 1.0, storage=2, far_precision=0, near_precision=3)
     assert ei.value.code == htlr.HTLR_EUNSUPPORTED
