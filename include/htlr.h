@@ -97,10 +97,13 @@ typedef enum {
                             |x| in [1e-30, 1e30], for that accuracy */
     HTLR_PREC_FP32 = 2,  /* FP32 blocks, products and accumulation (~1e-7 relative) */
     HTLR_PREC_BF16X6 = 3 /* tensor cores (tcgen05): operands split into three BF16 terms,
-                            the six products a_i b_j with i + j <= 4 accumulated in FP32
-                            (FP32-class accuracy); the many-right-hand-side path.  The far
-                            field in BF16X6 needs a BF16X6 or generated near field;
-                            right-hand sides are processed 64 at a time */
+                            the six products a_i b_j with i + j <= 4 (1-based) accumulated
+                            in FP32 tensor memory; the many-right-hand-side path, 64 RHS at
+                            a time.  The tensor cores' FP32 accumulation loses ~2e-8
+                            relative per accumulated MMA, so the error grows with the
+                            accumulation length (see tc_segment).  A BF16X6 far field goes
+                            with a BF16X6, generated, or held FP64/df64/FP32 near field;
+                            a BF16X6 near field needs a BF16X6 far field */
 } htlr_precision;
 
 typedef struct {
@@ -113,6 +116,11 @@ typedef struct {
     size_t hbm_limit;  /* maximum bytes the handle may allocate (0: 90% of free memory) */
     int far_precision;   /* htlr_precision of the admissible blocks (default FP64) */
     int near_precision;  /* htlr_precision of the inadmissible blocks (default FP64) */
+    int tc_segment;      /* BF16X6 with SHARED blocks: K steps of 16 columns accumulated in
+                            FP32 tensor memory before they are added to the FP64 result
+                            (0: default 8).  The FP32 accumulation of the tensor cores loses
+                            about 2^-25 relative per MMA, so shorter segments are more
+                            accurate and drain more often */
 } htlr_options;
 
 /* Statistics of a constructed operator (htlr_info). */

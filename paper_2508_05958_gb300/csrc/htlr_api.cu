@@ -179,9 +179,9 @@ static TcgShape tcg_shape(int Nd, int Kd)
     t.Nd = Nd;
     t.nch = (Kd + 15) / 16;
     t.Npad = (Nd + 15) / 16 * 16;
-    if (t.Npad > 256) t.Npad = (Nd + 31) / 32 * 32;   // two MMAs of Npad / 2 (a multiple of 16)
-    t.nN = t.Npad > 256 ? 2 : 1;
-    t.Nh = t.Npad / t.nN;
+    if (t.Npad > 256) t.Npad = (Nd + 31) / 32 * 32;   // two passes of Npad / 2 (a multiple of 16)
+    t.passes = t.Npad > 256 ? 2 : 1;
+    t.Nw = t.Npad / t.passes;
     t.NGb = t.Npad / 8;
     t.core_elems = (long long)t.nch * 3 * t.NGb * 128;
     t.box_elems = (long long)3 * t.nch * (kTcRpMax / 8) * 128;
@@ -1215,6 +1215,40 @@ LevelGeom level_geom(const htlr_handle *H, int lv)
 
 // One RHS chunk of HMultVec (stages: up, stream [+ generated near], reduce, out) with the
 // given scratch: W[lv], Hs[lv] per level, task partials, the kinds table.
+// The generated near field for all right-hand sides at once (its kernel values are
+// evaluated once per point pair and shared by up to 16 RHS per pass), written into f
+// before the chunks add their far fields.
+int launch_near_gen_all(const htlr_handle *H, const double *uc, double *fc, int nh, cudaStream_t s)
+{
+    if (!H->near_generated) return 0;
+    const int d = H->d, n = H->n, L = H->L;
+    const long long N = (long long)ipow(n, d);
+    int launches = 0;
+    {
+        NearGenArgs g{};
+        g.k = H->kern;
+        g.d = d;
+        g.n = n;
+        g.L = L;
+        g.nrhs = nh;
+        g.leafg = level_geom(H, L);
+        g.coords = H->d_coords;
+        g.width = H->d_width;
+        g.diag = H->d_diagpts;
+        g.a = H->d_a;
+        g.rowptr = H->d_near_rowptr;
+        g.col = H->d_near_col;
+        g.u = uc;
+        g.ldu = N;
+        g.f = fc;
+        g.ldf = N;
+        g.max_rows = H->max_leaf_rows;
+        launch_near_generated(H->near_prec, g, s);
+        launches += (nh + 15) / 16;
+    }
+    return launches;
+}
+
 int run_chunk(const htlr_handle *H, const KindDesc *d_kinds, double *part,
               const std::vector<double *> &W, const std::vector<double *> &Hs, const double *uc,
               double *fc, int nh, StageEvents *tev, cudaStream_t s)
@@ -1272,6 +1306,7 @@ int run_chunk(const htlr_handle *H, const KindDesc *d_kinds, double *part,
             TcgArgs g{};
             g.counter = counter;
             g.order = order;
+            g.seg_stages = H->tc_seg_stages;
             g.offs = reinterpret_cast<const int4 *>(cls);
             for (int c = 0; c < 8; ++c) {
                 g.cls_start[c] = cs[c];
@@ -1288,20 +1323,20 @@ int run_chunk(const htlr_handle *H, const KindDesc *d_kinds, double *part,
             g.Nd = tg.Nd;
             g.nch = tg.nch;
             g.NGb = tg.NGb;
-            g.Nh = tg.Nh;
-            g.nN = tg.nN;
+            g.Nw = tg.Nw;
+            g.passes = tg.passes;
             g.blocks = static_cast<const uint16_t *>(blocks);
             g.core_elems = tg.core_elems;
             g.tasks = H->d_tasks_tc;
             g.row_task = row_task;
             g.part = H->d_part_tc;
             g.ld = ld;
-            int S = (int)((200 * 1024) / tcg_stage_bytes(tg.NGb));
+            int S = (int)((200 * 1024) / tcg_stage_bytes(tg.Nw / 8));
             if (S > kTcMaxStages) S = kTcMaxStages;
             if (H->tc_stages_cap >= 2 && S > H->tc_stages_cap) S = H->tc_stages_cap;
             g.stages = S < 2 ? 2 : S;
             int cols = 32;
-            while (cols < tg.Npad) cols *= 2;
+            while (cols < 2 * tg.Nw) cols *= 2;   // two accumulator buffers
             g.tmem_cols = cols;
             g.err = H->d_err;
             launch_tc_group(g, tm.b, s);
@@ -1348,28 +1383,6 @@ int run_chunk(const htlr_handle *H, const KindDesc *d_kinds, double *part,
         for (int r0 = 0; r0 < nh; r0 += 4)
             launches += launch_streams(H, d_kinds, uc + (long long)r0 * N, N, std::min(4, nh - r0),
                                        part + (long long)r0 * H->near_ld, s);
-    }
-    if (H->near_generated) {
-        NearGenArgs g{};
-        g.k = H->kern;
-        g.d = d;
-        g.n = n;
-        g.L = L;
-        g.nrhs = nh;
-        g.leafg = level_geom(H, L);
-        g.coords = H->d_coords;
-        g.width = H->d_width;
-        g.diag = H->d_diagpts;
-        g.a = H->d_a;
-        g.rowptr = H->d_near_rowptr;
-        g.col = H->d_near_col;
-        g.u = uc;
-        g.ldu = N;
-        g.f = fc;
-        g.ldf = N;
-        g.max_rows = H->max_leaf_rows;
-        launch_near_generated(H->near_prec, g, s);
-        ++launches;
     }
     mark(5);
     mark(6);
@@ -1452,6 +1465,17 @@ static int enqueue_matvec(const htlr_handle *H, const double *u, double *f, int 
         Hs[lv] = H->lev[lv].d_H;
     }
     int launches = 0;
+    if (H->near_generated) {
+        if (tev) cudaEventRecord(tev->ev[4], st);
+        launches += launch_near_gen_all(H, u, f, nrhs, st);
+        if (tev) {
+            cudaEventRecord(tev->ev[5], st);
+            cudaEventSynchronize(tev->ev[5]);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, tev->ev[4], tev->ev[5]);
+            tev->ms[2] += ms;
+        }
+    }
     for (int c0 = 0; c0 < nrhs; c0 += H->nrc) {
         const int nh = std::min(H->nrc, nrhs - c0);
         launches += run_chunk(H, H->d_kinds, H->d_part, W, Hs, u + (long long)c0 * N,
@@ -1516,6 +1540,7 @@ int htlr_construct_ex(htlr_handle **out, const htlr_kernel *k, int d, int n, con
     }
     int q = (o && o->quad_order > 0) ? o->quad_order : 16;
     if (q > 64) return fail(HTLR_EINVAL, "quad_order must be in 1..64");
+    if (o && o->tc_segment < 0) return fail(HTLR_EINVAL, "tc_segment must be >= 0");
     if (o && (o->orth < -1 || o->orth > 1)) return fail(HTLR_EINVAL, "orth must be -1, 0 or 1");
     if (o && (o->far_precision < 0 || o->far_precision > 3 || o->near_precision < 0 ||
               o->near_precision > 3))
@@ -1542,6 +1567,7 @@ int htlr_construct_ex(htlr_handle **out, const htlr_kernel *k, int d, int n, con
     H->orth = (tensor || (o && o->orth == 0)) ? 0 : 1;
     H->far_prec = o ? o->far_precision : kPrecFP64;
     H->near_prec = o ? o->near_precision : kPrecFP64;
+    if (o && o->tc_segment > 0) H->tc_seg_stages = o->tc_segment;
     int rc;
     try {
         rc = build(H, grid, o);

@@ -79,9 +79,10 @@ struct TcShape {
 
 // Grouped tensor-core form of a SHARED block list (tc_group.cu): blocks Nd x Kd packed
 // as [chunk of 16 columns][split][row group][kcore][8][8], sources per box as
-// [split][chunk][row group][kcore][8][8]; the MMA's N (block rows) in nN pieces of Nh.
+// [split][chunk][row group][kcore][8][8]; the block rows (N) in `passes` passes of Nw
+// (Nw <= 256, so two accumulators of Nw columns fit in tensor memory).
 struct TcgShape {
-    int Kd = 0, Nd = 0, nch = 0, Npad = 0, NGb = 0, Nh = 0, nN = 0;
+    int Kd = 0, Nd = 0, nch = 0, Npad = 0, NGb = 0, Nw = 0, passes = 0;
     long long core_elems = 0;    // bf16 elements per packed block
     long long box_elems = 0;     // bf16 elements per packed source box at 64 RHS
 };
@@ -197,6 +198,7 @@ struct htlr_handle {
     // changes whenever the device-side task tables are rebuilt (captured plans re-capture)
     size_t task_bytes = 256 * 1024;
     int stream_ctas_per_sm = 8, stream_threads = 256, tc_stages_cap = 0;
+    int tc_seg_stages = 8;   // grouped tensor-core kernel: K stages per FP32 accumulation
     int generation = 0;
     htlr_stats stats{};
     std::vector<void *> allocs;
@@ -337,7 +339,7 @@ struct TcgArgs {
     int G, Rp, nr;                     // targets per group (G Rp = 128), padded / real RHS
     int nq;                            // groups along one parity line of dimension 1
     long long ngroups;
-    int Nd, nch, NGb, Nh, nN;
+    int Nd, nch, NGb, Nw, passes;
     const uint16_t *blocks;
     long long core_elems;
     const Task *tasks;
@@ -348,13 +350,14 @@ struct TcgArgs {
     int *err;
     int *counter;                      // next group (reset to 0 before each launch)
     const int *order;                  // groups, heaviest first
+    int seg_stages;                    // stages accumulated in TMEM before a drain to FP64
 };
 void launch_tcg_pack_blocks(const double *src, long long nblk, int ld, int Nd, int Kd, int nch,
                             int NGb, uint16_t *dst, cudaStream_t s);
 void launch_tcg_pack_x(const double *W, long long w_box_stride, int Kd, int nbox, int nr, int Rp,
                        int nch, int is_near, int d, int n, int leaf, int L, const double *u,
                        long long ldu, uint16_t *dst, cudaStream_t s);
-size_t tcg_stage_bytes(int NGb);
+size_t tcg_stage_bytes(int NGw);
 void launch_tc_group(const TcgArgs &a, const void *tmap, cudaStream_t s);
 int tcg_encode_source_map(void *tmap_out, const uint16_t *base, int nch, int Rp, int nb1, int d);
 // ---- tc_stream.cu: tensor-core (tcgen05) block stream for many right-hand sides ----

@@ -83,10 +83,11 @@ __device__ __forceinline__ T kv_eval(const KParams &k, int d, T r2, T dx0, T dx1
         if constexpr (sizeof(T) == 4) return (T)k.scale * rsqrtf(r2);
         else return k.scale / sqrt(r2);
     } else if constexpr (KT == HTLR_K_EXP_R) {
-        if constexpr (sizeof(T) == 4) return (T)k.scale * expf(-(r2 * rsqrtf(r2)));
+        if constexpr (sizeof(T) == 4) return (T)k.scale * __expf(-(r2 * rsqrtf(r2)));
         else return k.scale * exp(-sqrt(r2));
     } else if constexpr (KT == HTLR_K_GAUSS) {
-        return (T)k.scale * exp(-r2 * (T)k.inv2s2);
+        if constexpr (sizeof(T) == 4) return (T)k.scale * __expf(-r2 * (T)k.inv2s2);
+        else return k.scale * exp(-r2 * k.inv2s2);
     } else if constexpr (KT == HTLR_K_POLY) {
         const T dxs[3] = {dx0, dx1, dx2};
         T v = (T)k.scale;
@@ -111,6 +112,39 @@ __device__ __forceinline__ void sweep(const KParams &k, int d, int cols, bool se
                                       const T (&xr)[PER][3], const int (&irow)[PER],
                                       T (&acc)[PER][NR])
 {
+    if constexpr (sizeof(T) == 4 && NR % 2 == 0) {
+        // FP32: the multiply-adds of two right-hand sides in one packed FMA (f32x2)
+        float2 a2[PER][NR / 2];
+#pragma unroll
+        for (int m = 0; m < PER; ++m)
+#pragma unroll
+            for (int r = 0; r < NR / 2; ++r) a2[m][r] = make_float2(acc[m][2 * r], acc[m][2 * r + 1]);
+        const float2 *swu2 = reinterpret_cast<const float2 *>(swu);
+        for (int j = 0; j < cols; ++j) {
+            const T y0 = sy[4 * j], y1 = sy[4 * j + 1], y2 = sy[4 * j + 2];
+            float2 wu[NR / 2];
+#pragma unroll
+            for (int r = 0; r < NR / 2; ++r) wu[r] = swu2[j * (NR / 2) + r];
+#pragma unroll
+            for (int m = 0; m < PER; ++m) {
+                const T dx0 = xr[m][0] - y0, dx1 = xr[m][1] - y1, dx2 = xr[m][2] - y2;
+                const T r2 = dx0 * dx0 + dx1 * dx1 + dx2 * dx2;
+                T kv = kv_eval<T, KT>(k, d, r2, dx0, dx1, dx2);
+                kv = (self && j == irow[m]) ? (T)0 : kv;
+                const float2 kv2 = make_float2(kv, kv);
+#pragma unroll
+                for (int r = 0; r < NR / 2; ++r) a2[m][r] = __ffma2_rn(kv2, wu[r], a2[m][r]);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < PER; ++m)
+#pragma unroll
+            for (int r = 0; r < NR / 2; ++r) {
+                acc[m][2 * r] = a2[m][r].x;
+                acc[m][2 * r + 1] = a2[m][r].y;
+            }
+        return;
+    }
     for (int j = 0; j < cols; ++j) {
         const T y0 = sy[4 * j], y1 = sy[4 * j + 1], y2 = sy[4 * j + 2];
         T wu[NR];

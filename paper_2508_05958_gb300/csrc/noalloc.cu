@@ -61,6 +61,7 @@ struct StageEvents;
 int run_chunk(const htlr_handle *H, const KindDesc *d_kinds, double *part,
               const std::vector<double *> &W, const std::vector<double *> &Hs, const double *uc,
               double *fc, int nh, StageEvents *tev, cudaStream_t s);
+int launch_near_gen_all(const htlr_handle *H, const double *uc, double *fc, int nh, cudaStream_t s);
 
 int matvec_noalloc(const htlr_handle *H, const double *u, double *f, int nrhs)
 {
@@ -128,6 +129,7 @@ int matvec_noalloc(const htlr_handle *H, const double *u, double *f, int nrhs)
         W[lv] = reinterpret_cast<double *>(base + w_off[lv]);
         Hs[lv] = reinterpret_cast<double *>(base + h_off[lv]);
     }
+    launch_near_gen_all(H, u, f, nrhs, s);
     for (int c0 = 0; c0 < nrhs; c0 += H->nrc) {
         const int nh = nrhs - c0 < H->nrc ? nrhs - c0 : H->nrc;
         run_chunk(H, d_kinds, part, W, Hs, u + (long long)c0 * N, f + (long long)c0 * N, nh,

@@ -23,13 +23,25 @@
 // Both in the canonical K-major layout without swizzle: 8-row groups 256 bytes apart
 // (SBO), the two 8-column core matrices of a 16-column chunk 128 bytes apart (LBO).
 //
-// Roles: one thread of warp 1 issues the copies into an S-stage ring as soon as a stage
-// is free ("empty" mbarrier, committed by the MMAs that read it); one thread of warp 0
-// waits for each stage ("full" mbarrier, completed by the copies' byte count) and issues
-// its MMAs.  After a group the four warps read the accumulator with tcgen05.ld and write
-// the group's rows as FP64 partials.  Groups are taken heaviest first from an atomic
-// counter over a host-sorted order, so the SMs finish together.  Every wait is bounded:
-// on timeout the kernel records kDevTimeout, drains what it issued and frees TMEM.
+// Roles (10 warps):
+//   * one thread of warp 1 issues the copies into an S-stage ring as soon as a stage is
+//     free ("empty" mbarrier, committed by the MMAs that read it);
+//   * one thread of warp 0 waits for each stage ("full" mbarrier, completed by the
+//     copies' byte count) and issues its MMAs;
+//   * warps 2..9 drain the accumulator.
+// Accumulation is segmented, because the tensor cores' FP32 accumulation loses about
+// 2e-8 relative per accumulated MMA, with a bias, so the error grows with the number of
+// MMAs summed in one accumulator (7.6e-4 over a whole c3 row).  Every `seg_stages`
+// stages the MMA thread commits the segment and switches to the other of two TMEM
+// accumulator buffers (N <= 256 columns each; wider block lists are done in two passes
+// over N).  The drain warps read the finished buffer with tcgen05.ld, add it to FP32
+// sums held in their registers (two warps per TMEM lane quadrant, half the columns
+// each), and release the buffer.  The drain of one segment overlaps the MMAs of the
+// next.  At the end of a pass the sums are written as the FP64 partials of the group's
+// rows.
+// Groups are taken heaviest first from an atomic counter over a host-sorted order, so
+// the SMs finish together.  Every wait is bounded: on timeout the kernel records
+// kDevTimeout, drains what it issued and frees TMEM.
 #include <cuda.h>
 
 #include "tc_common.cuh"
@@ -40,7 +52,9 @@ using namespace tcc;
 
 namespace {
 
-constexpr int kGThreads = 128;
+constexpr int kGThreads = 320;        // MMA warp, copy warp, eight drain warps
+constexpr int kDrainThreads = 256;
+constexpr int kMaxDrainChunks = 16;   // 8-column chunks per drain thread (Nw <= 256)
 constexpr int kMaxGroupOffsets = 1024;
 
 }  // namespace
@@ -136,26 +150,50 @@ void launch_tcg_pack_x(const double *W, long long w_box_stride, int Kd, int nbox
 // ---------------------------------------------------------------------------------
 // The grouped stream.
 // ---------------------------------------------------------------------------------
+// Bounded wait that also gives up when another role of the CTA has aborted.
+__device__ __forceinline__ bool wait_or_abort(uint64_t *b, uint32_t parity, volatile int *abort_flag)
+{
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred P1;\n mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n"
+            " selp.b32 %0, 1, 0, P1;\n}"
+            : "=r"(done)
+            : "r"(smem_u32(b)), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (*abort_flag || clock64() - t0 > kWaitCycles) return false;
+    }
+}
+
 __global__ void __launch_bounds__(kGThreads, 1)
     tc_group_kernel(const __grid_constant__ CUtensorMap tmap, TcgArgs A)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
-    __shared__ uint64_t full_bar[kTcMaxStages], empty_bar[kTcMaxStages], done_bar;
+    __shared__ uint64_t full_bar[kTcMaxStages], empty_bar[kTcMaxStages];
+    __shared__ uint64_t seg_full[2], seg_empty[2], done_bar;
     __shared__ uint32_t tmem_holder, consumed;
     __shared__ volatile int abort_flag;
     __shared__ int n_valid, cur_group;
     __shared__ short valid_idx[kMaxGroupOffsets];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int S = A.stages, G = A.G, Rp = A.Rp, NGa = Rp / 8, nch = A.nch, NGb = A.NGb;
+    const int Nw = A.Nw, NGw = Nw / 8, passes = A.passes;
+    const long long F = A.seg_stages;                           // stages per segment
     const uint32_t a_split_bytes = 128u * 16u * 2u;             // 128 rows x 16 columns
     const uint32_t a_bytes = kSplits * a_split_bytes;
-    const uint32_t b_split_bytes = (uint32_t)NGb * 256u;        // Npad rows x 16 columns
+    const uint32_t b_split_bytes = (uint32_t)NGw * 256u;        // Nw rows x 16 columns
     const uint32_t b_bytes = kSplits * b_split_bytes;
     const uint32_t stage_bytes = a_bytes + b_bytes;
     if (tid == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(&full_bar[s], 1);
             mbar_init(&empty_bar[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&seg_full[b], 1);
+            mbar_init(&seg_empty[b], kDrainThreads);
         }
         mbar_init(&done_bar, 1);
         abort_flag = 0;
@@ -172,17 +210,26 @@ __global__ void __launch_bounds__(kGThreads, 1)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_holder;
-    // D f32, A and B bf16, both K-major, N = Nh, M = 128
-    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(A.Nh >> 3) << 17) |
+    // D f32, A and B bf16, both K-major, N = Nw, M = 128
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(Nw >> 3) << 17) |
                            ((uint32_t)(128 >> 4) << 24);
     const uint32_t lbo = 128, sbo = 256;
     const int pa[6] = {0, 0, 1, 0, 1, 2}, pb[6] = {0, 1, 0, 2, 1, 0};
     const int nb1 = A.nb1;
-    // stage counters run across groups: stage it % S, its use number it / S
-    uint32_t it_p = 0;       // loads issued (producer thread, tid 32)
+    // drain warps 2..9: TMEM lane quadrant warp % 4 (accumulator row m), and one half of
+    // the Nw columns of a pass each; their running sums stay in registers
+    const bool drainer = warp >= 2;
+    const int m = ((warp & 3) << 5) + lane;
+    const int half = (warp - 2) >> 2;
+    const int my_cols = Nw / 2, my_c0 = half * my_cols;   // a multiple of 8
+    const int nck = my_cols / 8;                          // <= kMaxDrainChunks
+    // counters run across groups
+    uint32_t it_p = 0;       // loads issued (producer, tid 32)
     uint32_t it_c = 0;       // stages consumed (MMA thread, tid 0)
+    uint32_t sc_m = 0;       // segments committed (MMA thread)
+    uint32_t sc_d = 0;       // segments drained (drain threads)
+    int done_pending = 0;
     uint32_t done_ph = 0;
-    int done_pending = 0;    // commits to done_bar not yet waited for (MMA thread)
     bool ok = true;
 
     while (true) {
@@ -214,114 +261,144 @@ __global__ void __launch_bounds__(kGThreads, 1)
                     v = s2 >= 0 && s2 < nb1 && (A.d == 2 || (s3 >= 0 && s3 < nb1)) &&
                         lo + 2 * (G - 1) >= 0 && lo < nb1;
                 }
-                const unsigned m = __ballot_sync(0xffffffffu, v);
-                if (v) valid_idx[cnt + __popc(m & ((1u << lane) - 1u))] = (short)i;
-                cnt += __popc(m);
+                const unsigned msk = __ballot_sync(0xffffffffu, v);
+                if (v) valid_idx[cnt + __popc(msk & ((1u << lane) - 1u))] = (short)i;
+                cnt += __popc(msk);
             }
             if (lane == 0) n_valid = cnt;
         }
         __syncthreads();
-        const long long total = (long long)n_valid * nch;
+        const long long total = (long long)n_valid * nch;          // stages per pass
+        const long long nseg = (total + F - 1) / F;                 // segments per pass
         if (tid == 32 && total > 0) {
             // producer: refill a stage as soon as the MMAs that read it are done
-            for (long long q = 0; q < total; ++q, ++it_p) {
-                const int s = (int)(it_p % S);
-                if (it_p >= (uint32_t)S && !mbar_wait(&empty_bar[s], ((it_p / S) - 1) & 1)) {
-                    abort_flag = 1;
-                    break;
-                }
-                if (abort_flag) break;
-                const int4 o = offs[valid_idx[(int)(q / nch)]];
-                const int ch = (int)(q % nch);
-                const int s0 = t0b1 + o.x;                 // b_1 of the first source
-                const int sc1 = s0 & 1;                    // (two's complement: also < 0)
-                const int sq0 = (s0 - sc1) / 2;
-                const int sb23 = (b2 + o.y) + nb1 * (b3 + o.z);
-                unsigned char *st = sm + (size_t)s * stage_bytes;
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
-                                 smem_u32(&full_bar[s])),
-                             "r"(stage_bytes)
-                             : "memory");
-                for (int a = 0; a < kSplits; ++a)
-                    tensor_load_5d(st + a * a_split_bytes, &tmap, 0, (a * nch + ch) * NGa, sc1,
-                                   sq0, sb23, &full_bar[s]);
-                const uint16_t *gb = A.blocks + (long long)o.w * A.core_elems +
-                                     (long long)ch * (b_bytes / 2);
-                bulk_load(st + a_bytes, gb, b_bytes, &full_bar[s]);
-            }
-        }
-        if (tid == 0 && total > 0) {
-            // MMA issue: the six split products into every N piece of the accumulator
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            for (long long q = 0; q < total; ++q, ++it_c) {
-                const int s = (int)(it_c % S);
-                if (!mbar_wait(&full_bar[s], (it_c / S) & 1)) {
-                    abort_flag = 1;
-                    break;
-                }
-                if (abort_flag) break;
-                const uint32_t a_base = smem_u32(sm + (size_t)s * stage_bytes);
-                const uint32_t b_base = a_base + a_bytes;
-                for (int pr = 0; pr < 6; ++pr) {
-                    const uint64_t ad = smem_desc(a_base + pa[pr] * a_split_bytes, lbo, sbo);
-                    for (int h = 0; h < A.nN; ++h) {
-                        const uint32_t b_addr =
-                            b_base + pb[pr] * b_split_bytes + (uint32_t)h * (uint32_t)(A.Nh / 8) * 256u;
-                        const uint32_t accumulate = (q == 0 && pr == 0) ? 0u : 1u;
-                        mma_bf16(tmem + (uint32_t)(h * A.Nh), ad, smem_desc(b_addr, lbo, sbo),
-                                 idesc, accumulate);
+            for (int ps = 0; ps < passes && !abort_flag; ++ps)
+                for (long long q = 0; q < total; ++q, ++it_p) {
+                    const int s = (int)(it_p % S);
+                    if (it_p >= (uint32_t)S &&
+                        !wait_or_abort(&empty_bar[s], ((it_p / S) - 1) & 1, &abort_flag)) {
+                        abort_flag = 1;
+                        break;
+                    }
+                    const int4 o = offs[valid_idx[(int)(q / nch)]];
+                    const int ch = (int)(q % nch);
+                    const int s0 = t0b1 + o.x;                 // b_1 of the first source
+                    const int sc1 = s0 & 1;                    // (two's complement: also < 0)
+                    const int sq0 = (s0 - sc1) / 2;
+                    const int sb23 = (b2 + o.y) + nb1 * (b3 + o.z);
+                    unsigned char *st = sm + (size_t)s * stage_bytes;
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                                     smem_u32(&full_bar[s])),
+                                 "r"(stage_bytes)
+                                 : "memory");
+                    for (int a = 0; a < kSplits; ++a)
+                        tensor_load_5d(st + a * a_split_bytes, &tmap, 0, (a * nch + ch) * NGa, sc1,
+                                       sq0, sb23, &full_bar[s]);
+                    const uint16_t *gb = A.blocks + (long long)o.w * A.core_elems +
+                                         (long long)ch * (kSplits * NGb * 128);
+                    if (passes == 1) {
+                        bulk_load(st + a_bytes, gb, b_bytes, &full_bar[s]);
+                    } else {
+                        for (int b = 0; b < kSplits; ++b)
+                            bulk_load(st + a_bytes + b * b_split_bytes,
+                                      gb + (long long)b * NGb * 128 + (long long)ps * NGw * 128,
+                                      b_split_bytes, &full_bar[s]);
                     }
                 }
-                mma_commit(&empty_bar[s]);
-            }
-            mma_commit(&done_bar);
-            ++done_pending;
+        }
+        if (tid == 0 && total > 0) {
+            // MMA issue: the six split products into the segment's accumulator buffer
+            for (int ps = 0; ps < passes && !abort_flag; ++ps)
+                for (long long q = 0; q < total; ++q, ++it_c) {
+                    const long long qs = q % F;
+                    const uint32_t buf = sc_m & 1;
+                    if (qs == 0) {
+                        // the buffer's previous segment must be drained before it is reset
+                        if (sc_m >= 2 &&
+                            !wait_or_abort(&seg_empty[buf], ((sc_m >> 1) - 1) & 1, &abort_flag)) {
+                            abort_flag = 1;
+                            break;
+                        }
+                        asm volatile("tcgen05.fence::after_thread_sync;");
+                    }
+                    const int s = (int)(it_c % S);
+                    if (!wait_or_abort(&full_bar[s], (it_c / S) & 1, &abort_flag)) {
+                        abort_flag = 1;
+                        break;
+                    }
+                    const uint32_t a_base = smem_u32(sm + (size_t)s * stage_bytes);
+                    const uint32_t b_base = a_base + a_bytes;
+                    for (int pr = 0; pr < 6; ++pr) {
+                        const uint32_t accumulate = (qs == 0 && pr == 0) ? 0u : 1u;
+                        mma_bf16(tmem + buf * (uint32_t)Nw,
+                                 smem_desc(a_base + pa[pr] * a_split_bytes, lbo, sbo),
+                                 smem_desc(b_base + pb[pr] * b_split_bytes, lbo, sbo), idesc,
+                                 accumulate);
+                    }
+                    mma_commit(&empty_bar[s]);
+                    if (qs == F - 1 || q == total - 1) {
+                        mma_commit(&seg_full[buf]);
+                        ++sc_m;
+                    }
+                }
             consumed = it_c;
+        }
+        if (drainer) {
+            // accumulator row m = k Rp + r: target tau_k = tau_0 + 2k e_1, RHS r
+            const int k = m / Rp, r = m % Rp;
+            const int tb1 = t0b1 + 2 * k;
+            double *out = nullptr;
+            if (tb1 < nb1 && r < A.nr) {
+                const int tau = tb1 + nb1 * b23;
+                const int ta = A.row_task[tau];
+                if (A.row_task[tau + 1] > ta) out = A.part + A.tasks[ta].part + (long long)r * A.ld;
+            }
+            for (int ps = 0; ps < passes; ++ps) {
+                float acc[kMaxDrainChunks * 8];
+#pragma unroll
+                for (int i = 0; i < kMaxDrainChunks * 8; ++i) acc[i] = 0.f;
+                for (long long sg = 0; sg < nseg; ++sg, ++sc_d) {
+                    const uint32_t buf = sc_d & 1;
+                    if (!wait_or_abort(&seg_full[buf], (sc_d >> 1) & 1, &abort_flag)) {
+                        abort_flag = 1;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    const uint32_t tbase = tmem + ((uint32_t)((warp & 3) * 32) << 16) +
+                                           buf * (uint32_t)Nw + (uint32_t)my_c0;
+#pragma unroll
+                    for (int c = 0; c < kMaxDrainChunks; ++c) {
+                        if (c < nck) {
+                            uint32_t v[8];
+                            asm volatile(
+                                "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]),
+                                  "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                                : "r"(tbase + (uint32_t)(8 * c)));
+                            asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+                            for (int jj = 0; jj < 8; ++jj) acc[8 * c + jj] += __uint_as_float(v[jj]);
+                        }
+                    }
+                    asm volatile("tcgen05.fence::before_thread_sync;");
+                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(
+                                     smem_u32(&seg_empty[buf]))
+                                 : "memory");
+                }
+                if (abort_flag) break;
+                if (out) {
+                    const int col0 = ps * Nw + my_c0;
+#pragma unroll
+                    for (int i = 0; i < kMaxDrainChunks * 8; ++i)
+                        if (i < my_cols && col0 + i < A.Nd) out[col0 + i] = (double)acc[i];
+                }
+            }
         }
         __syncthreads();
         if (abort_flag) {
             ok = false;
             break;
         }
-        // accumulator row m = k Rp + r: target tau_k = tau_0 + 2k e_1, right-hand side r
-        const int m = warp * 32 + lane, k = m / Rp, r = m % Rp;
-        const int tb1 = t0b1 + 2 * k;
-        double *out = nullptr;
-        if (tb1 < nb1 && r < A.nr) {
-            const int tau = tb1 + nb1 * b23;
-            const int ta = A.row_task[tau];
-            if (A.row_task[tau + 1] > ta) out = A.part + A.tasks[ta].part + (long long)r * A.ld;
-        }
-        if (total == 0) {
-            if (out)
-                for (int t = 0; t < A.Nd; ++t) out[t] = 0.0;
-            continue;
-        }
-        const int late = __syncthreads_or(mbar_wait(&done_bar, done_ph) ? 0 : 1);
-        done_ph ^= 1;
-        if (tid == 0) --done_pending;
-        if (late) {
-            if (tid == 0) atomicExch(A.err, (int)kDevTimeout);
-            ok = false;
-            break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        for (int c0 = 0; c0 < A.nN * A.Nh; c0 += 8) {
-            uint32_t v[8];
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
-                  "=r"(v[6]), "=r"(v[7])
-                : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;");
-            if (out)
-                for (int jj = 0; jj < 8; ++jj)
-                    if (c0 + jj < A.Nd) out[c0 + jj] = (double)__uint_as_float(v[jj]);
-        }
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;");
     }
     if (!ok) {
         if (tid == 0) {
@@ -348,13 +425,13 @@ __global__ void __launch_bounds__(kGThreads, 1)
                      "r"(A.tmem_cols));
 }
 
-size_t tcg_stage_bytes(int NGb) { return (size_t)kSplits * 128 * 16 * 2 + (size_t)kSplits * NGb * 256; }
+size_t tcg_stage_bytes(int NGw) { return (size_t)kSplits * 128 * 16 * 2 + (size_t)kSplits * NGw * 256; }
 
 void launch_tc_group(const TcgArgs &a, const void *tmap, cudaStream_t s)
 {
     if (a.ngroups <= 0) return;
     cudaMemsetAsync(a.counter, 0, sizeof(int), s);
-    const size_t smem = tcg_stage_bytes(a.NGb) * a.stages;
+    const size_t smem = tcg_stage_bytes(a.Nw / 8) * a.stages;
     cudaFuncSetAttribute(tc_group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int grid = a.ngroups < 152 ? (int)a.ngroups : 152;
     tc_group_kernel<<<grid, kGThreads, smem, s>>>(*static_cast<const CUtensorMap *>(tmap), a);

@@ -61,3 +61,36 @@ def test_c4_full_size_sampled_rows(oracle):
     assert rel(f[rows], ref) < TOL
     fm, _ = _run(w, u, grid=grid, far_precision=2, near_precision=0)
     assert rel(fm[rows], ref) < MIXED_TOL
+
+
+TC_TOL = 1e-5     # grouped tensor-core kernel, segmented accumulation (measured 1.8e-6)
+
+
+def test_c3_full_size_tensor_cores_64_rhs(oracle):
+    """c3 as its tensor-core bench variant runs it: 64 RHS, SHARED, BF16X6 far and near
+    on the grouped kernel; and the BF16X6 far field with a df64 near field."""
+    from paper_2508_05958_gb300.workloads import workload
+    w = workload("c3")
+    u = w.u(nrhs=64)
+    rows = w.sample_rows(4, seed=13)
+    ref = oracle.htlr_rows(w.d, w.n, w.ktype, w.leaf, w.p, w.eta, u, rows, a=w.a())
+    f, info = _run(w, u, storage=2, far_precision=3, near_precision=3)
+    assert info["tc_grouped"] == (1 << 2) | (1 << 3) | (1 << 4) | -(1 << 31)
+    assert rel(f[rows], ref) < TC_TOL
+    fn, _ = _run(w, u, storage=2, far_precision=3, near_precision=1)
+    assert rel(fn[rows], ref) < TC_TOL
+
+
+def test_c4_full_size_tensor_core_far_fp32_near(oracle):
+    """c4 as its bench variant runs it: 16 RHS, BF16X6 far field (grouped kernel on the
+    tensor grid's shared cores), FP32 generated near field."""
+    from paper_2508_05958_gb300.workloads import workload
+    w = workload("c4")
+    grid = w.grid()
+    u = w.u(nrhs=16)
+    rows = w.sample_rows(4, seed=14)
+    ref = oracle.htlr_rows(w.d, w.n, w.ktype, w.leaf, w.p, w.eta, u, rows, grid=grid,
+                           orth=False)
+    f, info = _run(w, u, grid=grid, far_precision=3, near_precision=2)
+    assert info["storage"] == 3 and info["tc_grouped"] == (1 << 2) | (1 << 3) | (1 << 4)
+    assert rel(f[rows], ref) < TC_TOL

@@ -164,9 +164,13 @@ MIXED_TOL = 1e-6
 FP32_TOL = 1e-5     # far and near fields both in FP32
 # tensor cores (three-way BF16 split, FP32 accumulation in tensor memory): the products
 # are FP32-class, but the accumulator's rounding error grows with the number of MMAs
-# summed into it (about 2e-8 relative per accumulation, measured); whole block rows of
-# the n = 32 workloads reach ~2e-4.  Stated tolerance of this mode: 1e-3
-TC_TOL = 1e-3
+# summed into it (about 2e-8 relative per accumulation, measured).  The grouped kernel
+# (SHARED) accumulates in segments of 8 K steps (48 MMAs) and sums the segments in FP32
+# registers: measured 1.8e-6 on the full c3.  Stated tolerance: 1e-5.  The per-row kernel
+# (STORED) accumulates a whole block row: ~1e-6 at these sizes, up to ~1e-3 for long
+# rows.  Stated tolerance: 1e-4 at the sizes tested here.
+TC_TOL = 1e-5
+TC_ROW_TOL = 1e-4
 
 
 @pytest.mark.parametrize("storage", [1, 2])
@@ -334,7 +338,7 @@ def test_tensor_core_stored_blocks_match_oracle(oracle, nrhs):
     f, info = gpu_matvec(w, u, storage=1, far_precision=3, near_precision=3)
     assert info["storage"] == 1 and info["tc_grouped"] == 0
     ref, _ = _oracle_htlr(oracle, w, u)
-    assert rel(f, ref) < TC_TOL
+    assert rel(f, ref) < TC_ROW_TOL
 
 
 def test_tensor_core_grouped_equals_per_row(oracle):
@@ -347,8 +351,8 @@ def test_tensor_core_grouped_equals_per_row(oracle):
     fs, is_ = gpu_matvec(w, u, storage=1, far_precision=3, near_precision=3)
     assert ig["tc_grouped"] != 0 and is_["tc_grouped"] == 0
     ref, _ = _oracle_htlr(oracle, w, u)
-    assert rel(fg, ref) < TC_TOL and rel(fs, ref) < TC_TOL
-    assert rel(fg, fs) < TC_TOL
+    assert rel(fg, ref) < TC_TOL and rel(fs, ref) < TC_ROW_TOL
+    assert rel(fg, fs) < TC_ROW_TOL
 
 
 @pytest.mark.parametrize("case", [dict(name="c1", over={}), dict(name="c3", over=dict(n=32)),
@@ -383,7 +387,7 @@ def test_tensor_core_far_with_held_cuda_core_near(oracle, storage, near, nrhs):
     f, info = gpu_matvec(w, u, storage=storage, far_precision=3, near_precision=near)
     assert info["far_precision"] == 3 and info["near_precision"] == near
     ref, _ = _oracle_htlr(oracle, w, u)
-    assert rel(f, ref) < TC_TOL
+    assert rel(f, ref) < (TC_TOL if storage == 2 else TC_ROW_TOL)
 
 
 def test_tensor_core_rejects_unsupported_mixes():
