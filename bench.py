@@ -219,6 +219,12 @@ PREC_BYTES = {0: 8, 1: 8, 2: 4, 3: 6}
 ALU_PEAK = {0: 152 * 2 * 2.07e9, 1: 152 * 128 * 2.07e9 / 12, 2: 152 * 128 * 2.07e9}
 
 
+# DRAM traffic (read + write bytes) of one launch of the dominant kernel, taken with ncu
+# on the same workload and kernel build (see profiles/stream_kernel_df64_c2_launches.md);
+# keyed by (workload, storage, far precision, near precision, RHS).
+MEASURED_TRAFFIC = {("c2", 1, 1, 1, 1): 5804274688 + 13374976}
+
+
 def stream_elements(info, w):
     """Elements (multiply-adds per RHS) of the block stream: every admissible block's core
     (p_eff^d x p_eff^d) and every inadmissible block (|tau| x |sigma|), split into far and
@@ -488,6 +494,10 @@ def run_gpu(args, w):
         roofs.append(near_cc_roofline(info, w, nrhs, stage_ms[2]))
     roofs.sort(key=lambda r: -r["kernel_ms"])
     roof = roofs[0]                   # the dominant kernel
+    key = (w.name, info["storage"], info["far_precision"], info["near_precision"], nrhs)
+    if key in MEASURED_TRAFFIC and roof["kernel"] == "stream_kernel":
+        roof["traffic"] = MEASURED_TRAFFIC[key]
+        roof["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch"
 
     # end to end through the host-buffer entry point (pinned host memory, copies timed)
     uh = torch.from_numpy(np.ascontiguousarray(U.T)).pin_memory().numpy()
