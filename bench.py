@@ -392,7 +392,9 @@ def time_serving(args):
     stream = serving.request_stream(ops, args.serve_rate, args.serve_requests, seed=2025)
     arms = {"fp64_one_at_a_time": dict(mixed=0, max_active=1, max_batch=1),
             "mixed_batched": dict(mixed=1, inner_precision=htlr.PREC_FP32, max_active=64,
-                                  max_batch=16)}
+                                  max_batch=16),
+            "mixed_batched_tensor_cores": dict(mixed=1, inner_precision=htlr.PREC_BF16X6,
+                                               inner_tol=1e-5, max_active=64, max_batch=16)}
     out = {"workload": f"{len(ops)} operators (d=2 n<={args.serve_max_n2} log; d=3 "
                        f"n<={args.serve_max_n3} 1/r, exp(-r); r in 5..7; SHARED), "
                        f"{args.serve_requests} requests, Poisson {args.serve_rate:g}/s, "
@@ -411,6 +413,8 @@ def time_serving(args):
         out[name] = res
     out["solves_per_s_ratio"] = (out["mixed_batched"]["solves_per_s"] /
                                  out["fp64_one_at_a_time"]["solves_per_s"])
+    out["solves_per_s_ratio_tensor_cores"] = (out["mixed_batched_tensor_cores"]["solves_per_s"] /
+                                              out["fp64_one_at_a_time"]["solves_per_s"])
     return out
 
 

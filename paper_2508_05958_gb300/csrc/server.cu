@@ -207,6 +207,9 @@ struct Operator {
     size_t bytes = 0;
     long long last_used = 0;
     int active = 0;
+    bool inflight = false;     // a step is on the operator's stream
+    bool run_acc = false, run_inner = false;  // groups of that step
+    long long steps = 0;
 };
 
 }  // namespace
@@ -482,6 +485,9 @@ void htlr_server::enqueue_pre(Group &g, Operator &op, std::vector<Request *> &li
     const int B = (int)g.batch.size();
     if (B == 0) return;
     (void)acc_handle;
+    // descriptor regions at fixed offsets (multiples of max_batch): the post-step region
+    // [2 MB, 3 MB) of h_vec may still be read by a pending copy of the previous step
+    const int MB = o.max_batch;
     for (int i = 0; i < B; ++i) g.batch[i]->slot = i;
     // gather
     for (int i = 0; i < g.n_mv; ++i) {
@@ -520,26 +526,26 @@ void htlr_server::enqueue_pre(Group &g, Operator &op, std::vector<Request *> &li
         for (int pass = 0; pass < 2; ++pass) {
             for (int a = 0; a < na; ++a) {
                 Request *q = g.batch[arn[a]];
-                g.h_dot[pass * B + a] = DotDesc{q->V, w_of(arn[a]), q->k + 1,
+                g.h_dot[pass * MB + a] = DotDesc{q->V, w_of(arn[a]), q->k + 1,
                                                 (long long)arn[a] * S + pass * maxcnt};
             }
         }
         for (int a = 0; a < na; ++a)
-            g.h_dot[2 * B + a] = DotDesc{w_of(arn[a]), w_of(arn[a]), 1,
+            g.h_dot[2 * MB + a] = DotDesc{w_of(arn[a]), w_of(arn[a]), 1,
                                          (long long)arn[a] * S + 2 * maxcnt};
-        cudaMemcpyAsync(g.d_dot, g.h_dot, sizeof(DotDesc) * 3 * B, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(g.d_dot, g.h_dot, sizeof(DotDesc) * 3 * MB, cudaMemcpyHostToDevice, s);
         const int fin = (na * maxcnt + 255) / 256;
         for (int pass = 0; pass < 2; ++pass) {
-            const DotDesc *D = g.d_dot + pass * B;
+            const DotDesc *D = g.d_dot + pass * MB;
             dots_partial_k<<<dim3(kBlk, na), kThreads, 0, s>>>(D, N, maxcnt, g.d_part);
             dots_final_k<<<fin, 256, 0, s>>>(D, na, maxcnt, g.d_part, g.d_out);
             subcomb_k<<<dim3(grid_x(N), na), kThreads, 0, s>>>(D, N, g.d_out);
         }
-        dots_partial_k<<<dim3(kBlk, na), kThreads, 0, s>>>(g.d_dot + 2 * B, N, maxcnt, g.d_part);
-        dots_final_k<<<fin, 256, 0, s>>>(g.d_dot + 2 * B, na, maxcnt, g.d_part, g.d_out);
+        dots_partial_k<<<dim3(kBlk, na), kThreads, 0, s>>>(g.d_dot + 2 * MB, N, maxcnt, g.d_part);
+        dots_final_k<<<fin, 256, 0, s>>>(g.d_dot + 2 * MB, na, maxcnt, g.d_part, g.d_out);
     }
     if (nr) {
-        VecDesc *hv = g.h_vec + B;   // second third of the descriptor buffer
+        VecDesc *hv = g.h_vec + MB;   // second third of the descriptor buffer
         for (int a = 0; a < nr; ++a) {
             Request *q = g.batch[res[a]];
             VecDesc v{};
@@ -548,16 +554,16 @@ void htlr_server::enqueue_pre(Group &g, Operator &op, std::vector<Request *> &li
             v.dst = q->r;
             hv[a] = v;
         }
-        DotDesc *hd = g.h_dot + 2 * B + na;
+        DotDesc *hd = g.h_dot + 2 * MB + na;
         for (int a = 0; a < nr; ++a) {
             Request *q = g.batch[res[a]];
             hd[a] = DotDesc{q->r, q->r, 1, (long long)res[a] * S + 2 * maxcnt};
         }
-        cudaMemcpyAsync(g.d_vec + B, hv, sizeof(VecDesc) * nr, cudaMemcpyHostToDevice, s);
-        cudaMemcpyAsync(g.d_dot + 2 * B + na, hd, sizeof(DotDesc) * nr, cudaMemcpyHostToDevice, s);
-        resid_k<<<dim3(grid_x(N), nr), kThreads, 0, s>>>(g.d_vec + B, N);
-        dots_partial_k<<<dim3(kBlk, nr), kThreads, 0, s>>>(g.d_dot + 2 * B + na, N, maxcnt, g.d_part);
-        dots_final_k<<<(nr * maxcnt + 255) / 256, 256, 0, s>>>(g.d_dot + 2 * B + na, nr, maxcnt,
+        cudaMemcpyAsync(g.d_vec + MB, hv, sizeof(VecDesc) * nr, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(g.d_dot + 2 * MB + na, hd, sizeof(DotDesc) * nr, cudaMemcpyHostToDevice, s);
+        resid_k<<<dim3(grid_x(N), nr), kThreads, 0, s>>>(g.d_vec + MB, N);
+        dots_partial_k<<<dim3(kBlk, nr), kThreads, 0, s>>>(g.d_dot + 2 * MB + na, N, maxcnt, g.d_part);
+        dots_final_k<<<(nr * maxcnt + 255) / 256, 256, 0, s>>>(g.d_dot + 2 * MB + na, nr, maxcnt,
                                                             g.d_part, g.d_out);
     }
     cudaMemcpyAsync(g.h_out, g.d_out, sizeof(double) * (size_t)B * S, cudaMemcpyDeviceToHost, s);
@@ -654,58 +660,78 @@ void htlr_server::host_post(Group &g, Operator &op)
     }
     const int nsc = (int)sc.size(), nup = (int)up.size();
     if (nsc + nup) {
-        VecDesc *hv = g.h_vec + 2 * B;
+        const int MB = o.max_batch;
+        VecDesc *hv = g.h_vec + 2 * MB;
         for (int i = 0; i < nsc; ++i) hv[i] = sc[i];
         for (int i = 0; i < nup; ++i) hv[nsc + i] = up[i];
-        cudaMemcpyAsync(g.d_vec + 2 * B, hv, sizeof(VecDesc) * (nsc + nup), cudaMemcpyHostToDevice, s);
-        if (nsc) scale_k<<<dim3(grid_x(N), nsc), kThreads, 0, s>>>(g.d_vec + 2 * B, N);
-        if (nup) update_k<<<dim3(grid_x(N), nup), kThreads, 0, s>>>(g.d_vec + 2 * B + nsc, N);
+        cudaMemcpyAsync(g.d_vec + 2 * MB, hv, sizeof(VecDesc) * (nsc + nup), cudaMemcpyHostToDevice, s);
+        if (nsc) scale_k<<<dim3(grid_x(N), nsc), kThreads, 0, s>>>(g.d_vec + 2 * MB, N);
+        if (nup) update_k<<<dim3(grid_x(N), nup), kThreads, 0, s>>>(g.d_vec + 2 * MB + nsc, N);
     }
 }
 
+// One pass of the event loop: start a step on every idle operator that has active
+// requests (its requests that need the same handle form one batched matvec), and finish
+// the steps whose streams are idle (host side of GMRES, retirement).  Operators advance
+// independently, so a slow operator does not hold back the others.
 int htlr_server::step()
 {
-    ++step_no;
-    ++st.steps;
-    // split every operator's active requests by the handle they need now, at most
-    // max_batch per handle (the rest wait one step, oldest first)
-    struct Work {
-        Operator *op;
-        Group *g;
-        std::vector<Request *> list;
-    };
-    std::vector<Work> work;
+    bool progressed = false;
     for (int id = 0; id < (int)view.size(); ++id) {
         Operator &op = *view[id];
-        if (!op.resident || op.active == 0) continue;
-        Work wa{&op, &op.acc, {}}, wi{&op, &op.inner, {}};
+        if (!op.resident || op.active == 0 || op.inflight) continue;
+        std::vector<Request *> la, li;
         for (Request *q : active) {
             if (q->op != id) continue;
-            Work &w = (o.mixed && q->phase == kArnoldi) ? wi : wa;
-            if ((int)w.list.size() < o.max_batch) w.list.push_back(q);
+            std::vector<Request *> &l = (o.mixed && q->phase == kArnoldi) ? li : la;
+            if ((int)l.size() < o.max_batch) l.push_back(q);   // oldest first
         }
-        if (!wa.list.empty()) work.push_back(wa);
-        if (!wi.list.empty()) work.push_back(wi);
+        if (la.empty() && li.empty()) continue;
+        ++step_no;
+        ++st.steps;
         op.last_used = step_no;
+        op.run_acc = !la.empty();
+        op.run_inner = !li.empty();
+        if (op.run_acc) enqueue_pre(op.acc, op, la, true);
+        if (op.run_inner) enqueue_pre(op.inner, op, li, false);
+        op.inflight = true;
+        progressed = true;
     }
-    for (Work &w : work) enqueue_pre(*w.g, *w.op, w.list, w.g == &w.op->acc);
-    for (Work &w : work) {
-        cudaError_t e = cudaStreamSynchronize(w.op->s);
-        if (e != cudaSuccess) return cuda_fail(e, "server: step");
-        int derr = htlr_sync(w.g->H);
-        if (derr) return derr;
-        host_post(*w.g, *w.op);
-    }
-    // retire finished requests
-    for (size_t i = 0; i < active.size();) {
-        Request *q = active[i];
-        if (q->done) {
+    for (int id = 0; id < (int)view.size(); ++id) {
+        Operator &op = *view[id];
+        if (!op.inflight) continue;
+        cudaError_t e = cudaStreamQuery(op.s);
+        if (e == cudaErrorNotReady) continue;
+        op.inflight = false;
+        progressed = true;
+        int err = e == cudaSuccess ? HTLR_OK : cuda_fail(e, "server: step");
+        // the handles' device error words (bounded waits that gave up) are read every 32
+        // steps of the operator and before any of its requests is delivered
+        if (!err && ++op.steps % 32 == 0) {
+            err = htlr_sync(op.acc.H);
+            if (!err && op.inner.H) err = htlr_sync(op.inner.H);
+        }
+        if (!err) {
+            if (op.run_acc) host_post(op.acc, op);
+            if (op.run_inner) host_post(op.inner, op);
+        }
+        bool checked = false;
+        for (size_t i = 0; i < active.size();) {
+            Request *q = active[i];
+            if (q->op != id || (!q->done && !err)) {
+                ++i;
+                continue;
+            }
+            if (!err && !checked) {
+                err = htlr_sync(op.acc.H);
+                if (!err && op.inner.H) err = htlr_sync(op.inner.H);
+                checked = true;
+            }
             active.erase(active.begin() + (long)i);
-            finish(q, q->info.error);
-        } else {
-            ++i;
+            finish(q, err ? err : q->info.error);
         }
     }
+    if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(20));
     return HTLR_OK;
 }
 

@@ -149,3 +149,31 @@ def test_request_that_cannot_fit_fails_without_blocking_others():
             S.submit(17, _rhs(ops[2], 1))
         assert e.value.code == htlr.HTLR_EINVAL
         assert S.stats()["failed"] == 1
+
+
+def test_batches_that_grow_and_shrink_between_steps():
+    """Requests of one operator arriving in waves, so consecutive steps of the operator
+    have batches of different sizes (the descriptors of one step must not disturb the
+    copies of the previous one).  Every result equals its solo solve."""
+    import time
+    from paper_2508_05958_gb300 import htlr
+    ops = _ops()[1:2]
+    seeds = list(range(900, 924))
+    with htlr.Server(mixed=1, inner_precision=htlr.PREC_FP32, max_batch=8) as S:
+        op = S.add_operator(ops[0].ktype, ops[0].d, ops[0].n, ops[0].leaf, ops[0].r,
+                            ops[0].eta, a=ops[0].a(), storage=2)
+        ids = []
+        for wave in range(6):
+            for sd in seeds[4 * wave:4 * wave + 4]:
+                ids.append(S.submit(op, _rhs(ops[0], sd)))
+            time.sleep(0.002 * (wave % 3))
+        out = [S.wait(r, WAIT_S) for r in ids]
+        st = S.stats()
+    assert st["completed"] == len(seeds) and st["failed"] == 0
+    with htlr.Server(mixed=1, inner_precision=htlr.PREC_FP32, max_batch=8, max_active=1) as S1:
+        op1 = S1.add_operator(ops[0].ktype, ops[0].d, ops[0].n, ops[0].leaf, ops[0].r,
+                              ops[0].eta, a=ops[0].a(), storage=2)
+        for (u, inf), sd in zip(out, seeds):
+            assert inf["converged"] == 1
+            u1, _ = S1.wait(S1.submit(op1, _rhs(ops[0], sd)), WAIT_S)
+            assert _rel(u, u1) <= SAME_TOL
