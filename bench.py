@@ -349,16 +349,18 @@ def time_gmres(w, solves, stream):
     import torch
     from paper_2508_05958_gb300 import htlr
     out = {}
+    # operators held SHARED (one block per offset): the faster single-RHS form for every
+    # precision here, the plain FP64 baseline included
     variants = {"fp64": ((0, 0), None), "mixed_refined": ((1, 1), (2, 1))}
     for name, (acc, inner) in variants.items():
         H = htlr.htlr_construct(w.ktype, w.d, w.n, w.leaf, w.p, w.eta, kscale=w.kscale,
                                 kparam=w.kparam, a=w.a(), far_precision=acc[0],
-                                near_precision=acc[1], stream=stream)
+                                near_precision=acc[1], stream=stream, storage=2)
         Hi = None
         if inner:
             Hi = htlr.htlr_construct(w.ktype, w.d, w.n, w.leaf, w.p, w.eta, kscale=w.kscale,
                                      kparam=w.kparam, a=w.a(), far_precision=inner[0],
-                                     near_precision=inner[1], stream=stream)
+                                     near_precision=inner[1], stream=stream, storage=2)
         f = torch.from_numpy(np.ascontiguousarray(w.u(nrhs=1, seed=500).T)).cuda()
         u = torch.zeros_like(f)
         htlr.htlr_gmres(H, f, u, 1, H_inner=Hi)          # warm-up

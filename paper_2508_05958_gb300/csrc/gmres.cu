@@ -117,9 +117,11 @@ struct Work {
     double *e = nullptr;     // nrhs x N (refinement correction)
     double *part = nullptr;  // kDotBlocks x nrhs x (m + 1)
     double *c = nullptr;     // nrhs x (m + 1)
+    double *c2 = nullptr;    // nrhs x (m + 1): second Gram-Schmidt pass
+    double *nn = nullptr;    // nrhs: squared norms
     ~Work()
     {
-        for (double *p : {V, w, r, e, part, c})
+        for (double *p : {V, w, r, e, part, c, c2, nn})
             if (p) cudaFree(p);
     }
 };
@@ -188,14 +190,21 @@ int gmres_solve(const htlr_handle *A, Work &W, const double *b, double *x, doubl
             double *Vk = W.V + (long long)k * nrhs * N;
             if ((rc = matvec_enqueue(A, Vk, W.w, nrhs))) return rc;
             ++matvecs;
-            // CGS2: h = V^T w, w -= V h, twice
-            std::vector<double> h1, h2;
-            if ((rc = dots(W, s, W.V, W.w, k + 1, W.c, &h1))) return rc;
+            // CGS2: h = V^T w, w -= V h, twice; then ||w||^2.  The coefficients stay on the
+            // device between the passes; the host reads them once per step
+            if ((rc = dots(W, s, W.V, W.w, k + 1, W.c, nullptr))) return rc;
             sub_combination<<<kGrid, kThreads, 0, s>>>(N, nrhs, k + 1, W.V, W.c, W.w);
-            if ((rc = dots(W, s, W.V, W.w, k + 1, W.c, &h2))) return rc;
-            sub_combination<<<kGrid, kThreads, 0, s>>>(N, nrhs, k + 1, W.V, W.c, W.w);
-            std::vector<double> nn;
-            if ((rc = dots(W, s, W.w, W.w, 1, W.c, &nn))) return rc;
+            if ((rc = dots(W, s, W.V, W.w, k + 1, W.c2, nullptr))) return rc;
+            sub_combination<<<kGrid, kThreads, 0, s>>>(N, nrhs, k + 1, W.V, W.c2, W.w);
+            if ((rc = dots(W, s, W.w, W.w, 1, W.nn, nullptr))) return rc;
+            std::vector<double> h1((size_t)nrhs * (k + 1)), h2(h1.size()), nn((size_t)nrhs);
+            cudaMemcpyAsync(h1.data(), W.c, sizeof(double) * h1.size(), cudaMemcpyDeviceToHost, s);
+            cudaMemcpyAsync(h2.data(), W.c2, sizeof(double) * h2.size(), cudaMemcpyDeviceToHost, s);
+            cudaMemcpyAsync(nn.data(), W.nn, sizeof(double) * nn.size(), cudaMemcpyDeviceToHost, s);
+            {
+                cudaError_t e = cudaStreamSynchronize(s);
+                if (e != cudaSuccess) return cuda_fail(e, "gmres step");
+            }
             bool all_conv = true;
             for (int r = 0; r < nrhs; ++r) {
                 double *hc = &Hh[((size_t)r * m + k) * (m + 1)];
@@ -301,7 +310,9 @@ extern "C" int htlr_gmres(const htlr_handle *H, const htlr_handle *H_inner, cons
         (e = cudaMalloc(&W.w, sizeof(double) * vec)) != cudaSuccess ||
         (e = cudaMalloc(&W.r, sizeof(double) * vec)) != cudaSuccess ||
         (e = cudaMalloc(&W.part, sizeof(double) * kDotBlocks * nrhs * (W.m + 1))) != cudaSuccess ||
-        (e = cudaMalloc(&W.c, sizeof(double) * nrhs * (W.m + 1))) != cudaSuccess)
+        (e = cudaMalloc(&W.c, sizeof(double) * nrhs * (W.m + 1))) != cudaSuccess ||
+        (e = cudaMalloc(&W.c2, sizeof(double) * nrhs * (W.m + 1))) != cudaSuccess ||
+        (e = cudaMalloc(&W.nn, sizeof(double) * nrhs)) != cudaSuccess)
         return cuda_fail(e, "htlr_gmres workspace");
     int iters = 0, matvecs = 0, refinements = 0, rc;
     std::vector<double> rel;
