@@ -247,39 +247,13 @@ def stream_elements(info, w):
     return far, near, far_unique, near_unique
 
 
-def tc_tensor_flops(info, w, nrhs):
-    """BF16 tensor-core FLOPs the BF16X6 stream executes for one RHS chunk: six MMAs per
-    multiply-add on padded tiles (128-row M-tiles, K padded to the chunk, N = RHS rounded
-    up to 16)."""
-    def shape(rows):
-        mt = (rows + 127) // 128
-        kc = 16
-        for k in (64, 32, 16):
-            stage = 3 * mt * 128 * k * 2 + 3 * 64 * k * 2
-            kc = k
-            if stage * 3 <= 210 * 1024:
-                break
-        return mt * 128, -(-rows // kc) * kc
-    rp = -(-min(nrhs, 64) // 16) * 16
-    total = 0.0
-    for lv, nfar in enumerate(info["far_per_level"]):
-        if nfar:
-            pd = min(w.p, w.n >> lv) ** w.d
-            m, k = shape(pd)
-            total += nfar * 12.0 * m * k * rp
-    if info["near_precision"] == 3:
-        m, k = shape(w.leaf ** w.d)
-        total += info["near_blocks"] * 12.0 * m * k * rp
-    return total * -(-nrhs // 64)
-
-
 def stream_roofline(info, w, nrhs, stream_ms, hbm_peak, hbm_src, bf16_peak=None,
                     executed_flops=None):
     fp, np_ = info["far_precision"], info["near_precision"]
     if fp == 3:
         far, near, far_u, near_u = stream_elements(info, w)
         t = stream_ms * 1e-3
-        executed = executed_flops if executed_flops else tc_tensor_flops(info, w, nrhs)
+        executed = executed_flops          # htlr_tensor_flops: MMAs the matvec issues
         peak = bf16_peak or 1895.3
         useful = 2.0 * (far + (near if np_ == 3 else 0.0)) * nrhs
         held = far_u * PREC_BYTES[fp] + (near_u * PREC_BYTES[np_] if info["storage"] != 3 else 0)

@@ -74,23 +74,24 @@ struct KParams {
     int deg;
 };
 
+// Kernel values without the kernel's scale factor, which the sweep folds into w_j u_j.
 template <typename T, int KT>
 __device__ __forceinline__ T kv_eval(const KParams &k, int d, T r2, T dx0, T dx1, T dx2)
 {
     if constexpr (KT == HTLR_K_LOG) {
-        return (T)k.scale * (T)0.5 * log(r2);
+        return (T)0.5 * log(r2);
     } else if constexpr (KT == HTLR_K_INV_R) {
-        if constexpr (sizeof(T) == 4) return (T)k.scale * rsqrtf(r2);
-        else return k.scale / sqrt(r2);
+        if constexpr (sizeof(T) == 4) return rsqrtf(r2);
+        else return 1.0 / sqrt(r2);
     } else if constexpr (KT == HTLR_K_EXP_R) {
-        if constexpr (sizeof(T) == 4) return (T)k.scale * __expf(-(r2 * rsqrtf(r2)));
-        else return k.scale * exp(-sqrt(r2));
+        if constexpr (sizeof(T) == 4) return __expf(-(r2 * rsqrtf(r2)));
+        else return exp(-sqrt(r2));
     } else if constexpr (KT == HTLR_K_GAUSS) {
-        if constexpr (sizeof(T) == 4) return (T)k.scale * __expf(-r2 * (T)k.inv2s2);
-        else return k.scale * exp(-r2 * k.inv2s2);
+        if constexpr (sizeof(T) == 4) return __expf(-r2 * (T)k.inv2s2);
+        else return exp(-r2 * k.inv2s2);
     } else if constexpr (KT == HTLR_K_POLY) {
         const T dxs[3] = {dx0, dx1, dx2};
-        T v = (T)k.scale;
+        T v = (T)1;
 #pragma unroll
         for (int l = 0; l < 3; ++l) {
             if (l < d) {
@@ -102,12 +103,12 @@ __device__ __forceinline__ T kv_eval(const KParams &k, int d, T r2, T dx0, T dx1
         }
         return v;
     } else {
-        return (T)k.scale;
+        return (T)1;
     }
 }
 
-template <typename T, int NR, int PER, int KT>
-__device__ __forceinline__ void sweep(const KParams &k, int d, int cols, bool self,
+template <typename T, int NR, int PER, int KT, bool SELF>
+__device__ __forceinline__ void sweep(const KParams &k, int d, int cols,
                                       const T *__restrict__ sy, const T *__restrict__ swu,
                                       const T (&xr)[PER][3], const int (&irow)[PER],
                                       T (&acc)[PER][NR])
@@ -130,7 +131,7 @@ __device__ __forceinline__ void sweep(const KParams &k, int d, int cols, bool se
                 const T dx0 = xr[m][0] - y0, dx1 = xr[m][1] - y1, dx2 = xr[m][2] - y2;
                 const T r2 = dx0 * dx0 + dx1 * dx1 + dx2 * dx2;
                 T kv = kv_eval<T, KT>(k, d, r2, dx0, dx1, dx2);
-                kv = (self && j == irow[m]) ? (T)0 : kv;
+                if constexpr (SELF) kv = j == irow[m] ? (T)0 : kv;   // diagonal: added apart
                 const float2 kv2 = make_float2(kv, kv);
 #pragma unroll
                 for (int r = 0; r < NR / 2; ++r) a2[m][r] = __ffma2_rn(kv2, wu[r], a2[m][r]);
@@ -155,7 +156,7 @@ __device__ __forceinline__ void sweep(const KParams &k, int d, int cols, bool se
             const T dx0 = xr[m][0] - y0, dx1 = xr[m][1] - y1, dx2 = xr[m][2] - y2;
             const T r2 = dx0 * dx0 + dx1 * dx1 + dx2 * dx2;
             T kv = kv_eval<T, KT>(k, d, r2, dx0, dx1, dx2);
-            kv = (self && j == irow[m]) ? (T)0 : kv;   // the diagonal is added separately
+            if constexpr (SELF) kv = j == irow[m] ? (T)0 : kv;   // the diagonal is added apart
 #pragma unroll
             for (int r = 0; r < NR; ++r) acc[m][r] += kv * wu[r];
         }
@@ -252,18 +253,22 @@ __global__ void __launch_bounds__(256) near_gen_kernel(NearGenArgs A, int r0, in
             sy[4 * j + 3] = (T)0;
 #pragma unroll
             for (int r = 0; r < NR; ++r)
-                swu[j * NR + r] = r < nr ? (T)(w * A.u[na + A.ldu * (r0 + r)]) : (T)0;
+                swu[j * NR + r] = r < nr ? (T)(A.k.scale * w * A.u[na + A.ldu * (r0 + r)]) : (T)0;
         }
         __syncthreads();
         const bool self = (sg == tau);
+#define HTLR_SWEEP(KT)                                                                 \
+    (self ? sweep<T, NR, PER, KT, true>(kp, d, cols, sy, swu, xr, irow, acc)           \
+          : sweep<T, NR, PER, KT, false>(kp, d, cols, sy, swu, xr, irow, acc))
         switch (A.k.type) {
-        case HTLR_K_LOG: sweep<T, NR, PER, HTLR_K_LOG>(kp, d, cols, self, sy, swu, xr, irow, acc); break;
-        case HTLR_K_INV_R: sweep<T, NR, PER, HTLR_K_INV_R>(kp, d, cols, self, sy, swu, xr, irow, acc); break;
-        case HTLR_K_EXP_R: sweep<T, NR, PER, HTLR_K_EXP_R>(kp, d, cols, self, sy, swu, xr, irow, acc); break;
-        case HTLR_K_GAUSS: sweep<T, NR, PER, HTLR_K_GAUSS>(kp, d, cols, self, sy, swu, xr, irow, acc); break;
-        case HTLR_K_POLY: sweep<T, NR, PER, HTLR_K_POLY>(kp, d, cols, self, sy, swu, xr, irow, acc); break;
-        default: sweep<T, NR, PER, HTLR_K_CONST>(kp, d, cols, self, sy, swu, xr, irow, acc); break;
+        case HTLR_K_LOG: HTLR_SWEEP(HTLR_K_LOG); break;
+        case HTLR_K_INV_R: HTLR_SWEEP(HTLR_K_INV_R); break;
+        case HTLR_K_EXP_R: HTLR_SWEEP(HTLR_K_EXP_R); break;
+        case HTLR_K_GAUSS: HTLR_SWEEP(HTLR_K_GAUSS); break;
+        case HTLR_K_POLY: HTLR_SWEEP(HTLR_K_POLY); break;
+        default: HTLR_SWEEP(HTLR_K_CONST); break;
         }
+#undef HTLR_SWEEP
     }
 #pragma unroll
     for (int m = 0; m < PER; ++m) {
