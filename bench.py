@@ -54,6 +54,24 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(ms, world, device):
+    """The slowest rank's step time (ms): every replica's work counts only when all are
+    done.  Collective over the default process group when world > 1."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world, N, nrhs, ms):
+    """Whole-job Gpts*RHS/s of `world` replicas, each applying the operator to N x nrhs
+    values per step of `ms` milliseconds (weak scaling: fixed work per GPU)."""
+    return world * N * nrhs / (ms * 1e-3) / 1e9
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -459,12 +477,8 @@ def run_gpu(args, w):
         dist.barrier()
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    ms = float(np.mean(step_ms))
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * w.N * nrhs / (ms * 1e-3) / 1e9
+    ms = max_over_ranks(float(np.mean(step_ms)), world, "cuda")
+    value = replica_throughput(world, w.N, nrhs, ms)
     stage_ms = stage / args.steps
 
     # roofline of the dominant kernel (the block stream)
