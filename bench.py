@@ -86,8 +86,16 @@ def dtype_name(info):
 
 def workload_desc(w, storage_name):
     kern = {0: "log|x-y|", 1: "1/|x-y|", 2: "exp(-|x-y|)", 3: "gauss", 4: "poly", 5: "const"}[w.ktype]
-    return (f"{w.name}: d={w.d} n={w.n} N={w.N} kernel {kern} a={w.a_kind} leaf {w.leaf}^{w.d} "
-            f"p={w.p} eta={w.eta:.4g} nrhs={w.nrhs} {storage_name}")
+    grid = "uniform grid" if w.grid_kind == "uniform" else "quasi-uniform tensor grid"
+    return (f"{w.name}: d={w.d} n={w.n} N={w.N} {grid} kernel {kern} a={w.a_kind} "
+            f"leaf {w.leaf}^{w.d} p={w.p} eta={w.eta:.4g} nrhs={w.nrhs} {storage_name}")
+
+
+def oracle_args(w):
+    """Grid arguments of the oracle's HTLR for a workload (tensor grids: no QR)."""
+    if w.grid_kind == "uniform":
+        return {}
+    return {"grid": w.grid(), "orth": False}
 
 
 # ----------------------------------------------------------------------------------
@@ -152,7 +160,7 @@ def time_oracle(w, budget_s):
     construction.  Returns (Gpts*RHS/s, cores, sample description, seconds)."""
     import oracle
     t0 = time.perf_counter()
-    H = oracle.HTLR(w.d, w.n, w.ktype, w.leaf, w.p, w.eta, a=w.a(), scale=w.kscale,
+    H = oracle.HTLR(w.d, w.n, w.ktype, w.leaf, w.p, w.eta, a=w.a(), scale=w.kscale, **oracle_args(w),
                     param=w.kparam)
     t_con = time.perf_counter() - t0
     u = w.u(nrhs=1)
@@ -182,7 +190,8 @@ def run_reference(args, w):
     oracle.build()
     import oracle as O
     t0 = time.perf_counter()
-    H = O.HTLR(w.d, w.n, w.ktype, w.leaf, w.p, w.eta, a=w.a(), scale=w.kscale, param=w.kparam)
+    H = O.HTLR(w.d, w.n, w.ktype, w.leaf, w.p, w.eta, a=w.a(), scale=w.kscale, param=w.kparam,
+               **oracle_args(w))
     t_con = time.perf_counter() - t0
     u = np.ascontiguousarray(w.u(nrhs=1)[:, 0])
     f = np.zeros(w.N)
@@ -433,7 +442,8 @@ def run_gpu(args, w):
 
     t0 = time.perf_counter()
     H = htlr.htlr_construct(w.ktype, w.d, w.n, w.leaf, w.p, w.eta, kscale=w.kscale,
-                            kparam=w.kparam, a=w.a(), storage=args.storage, stream=stream,
+                            kparam=w.kparam, a=w.a(), grid=w.grid(), storage=args.storage,
+                            stream=stream,
                             far_precision=args.far_precision, near_precision=args.near_precision)
     torch.cuda.synchronize()
     construct_s = time.perf_counter() - t0

@@ -129,6 +129,10 @@ CONFIGS = {
     # block shapes (216 x 216, 512 x 512) with ~0.3 GB of vectors, for profiling captures
     "c3_n64": Workload("c3_n64", d=3, n=64, ktype=K_INV_R, leaf=8, p=6, eta=1.0, nrhs=64,
                        a_kind="zero", u_kind="normal", seed=3),
+    # the c4 operator one level shallower (N = 262144, 16 RHS, quasi-uniform tensor grid):
+    # the same 343-row cores and 7-9 point leaves, for profiling captures
+    "c4_n64": Workload("c4_n64", d=3, n=64, ktype=K_EXP_R, leaf=8, p=7, eta=1.0, nrhs=16,
+                       a_kind="zero", u_kind="normal", grid_kind="quasi", seed=4),
 }
 
 
