@@ -101,7 +101,12 @@ typedef enum {
                             in FP32 tensor memory; the many-right-hand-side path, 64 RHS at
                             a time.  The tensor cores' FP32 accumulation loses ~2e-8
                             relative per accumulated MMA, so the error grows with the
-                            accumulation length (see tc_segment).  A BF16X6 far field goes
+                            accumulation length.  With SHARED blocks the accumulation runs
+                            in segments of tc_segment K steps whose sums are added in FP32
+                            registers (measured 1.8e-6 relative on the n = 128 operator);
+                            with STORED blocks a whole block row accumulates in tensor
+                            memory (~1e-6 on small operators, up to ~1e-3 on long rows).
+                            A BF16X6 far field goes
                             with a BF16X6, generated, or held FP64/df64/FP32 near field;
                             a BF16X6 near field needs a BF16X6 far field */
 } htlr_precision;
@@ -109,7 +114,8 @@ typedef enum {
 typedef struct {
     int storage;       /* htlr_storage (default AUTO) */
     int orth;          /* 1: QR-orthonormalise the factors (Algorithm 1), 0: keep the
-                          interpolation factors; -1: default (1) */
+                          interpolation factors; -1: default (1 on the uniform grid, 0 on
+                          tensor grids, which support only 0) */
     int quad_order;    /* Gauss-Legendre points per dimension and sub-box for the diagonal
                           integral (default 16, range 1..64) */
     void *stream;      /* cudaStream_t for construction and matvecs (NULL: default stream) */
