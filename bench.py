@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--gmres-solves", type=int, default=20,
                     help="GMRES solves (to 1e-10) timed after the matvec, per variant")
     ap.add_argument("--cpu-sample-s", type=float, default=20.0)
+    ap.add_argument("--paper-tables", action="store_true",
+                    help="construct and apply the settings of the paper's Tables 5.1-5.4 "
+                         "(context run; prints its own JSON line)")
+    ap.add_argument("--paper-max-n-points", type=int, default=1 << 22)
     ap.add_argument("--autotune-ms", type=float, default=2000.0,
                     help="htlr_autotune budget before timing (0: keep the default shapes)")
     ap.add_argument("--serve-requests", type=int, default=120,
@@ -566,8 +570,79 @@ def run_gpu(args, w):
         dist.destroy_process_group()
 
 
+# Settings of the paper's Tables 5.1-5.4 (§5.2, §5.3): table, kernel, d, n, leaf, p,
+# admissibility, storage m_h (GB) and MATLAB construction time t_c (s) as printed there
+# (one Xeon Gold 6226R).  Gaussian sigma = sqrt(d); SLP = -log r / (2 pi) in 2D and
+# 1 / (4 pi r) in 3D; strong admissibility = non-adjacent (eta = sqrt(d)); a = 0.
+PAPER_ROWS = [
+    ("5.1", "gauss", 2, 256, 16, 8, "weak", 0.16, 1.5), ("5.1", "gauss", 2, 512, 16, 8, "weak", 0.65, 3.8),
+    ("5.1", "gauss", 2, 1024, 16, 8, "weak", 2.6, 16), ("5.1", "gauss", 2, 2048, 16, 8, "weak", 10, 68),
+    ("5.1", "gauss", 2, 4096, 16, 8, "weak", 41, 280), ("5.1", "gauss", 2, 8192, 16, 8, "weak", 170, 1100),
+    ("5.2", "slp", 2, 256, 16, 8, "strong", 1.3, 7.6), ("5.2", "slp", 2, 512, 16, 8, "strong", 5.4, 30),
+    ("5.2", "slp", 2, 1024, 16, 8, "strong", 23, 130), ("5.2", "slp", 2, 2048, 16, 8, "strong", 92, 540),
+    ("5.2", "slp", 2, 4096, 16, 8, "strong", 370, 2100),
+    ("5.3", "gauss", 3, 32, 4, 4, "weak", 0.14, 4.0), ("5.3", "gauss", 3, 64, 4, 4, "weak", 1.2, 27),
+    ("5.3", "gauss", 3, 128, 4, 4, "weak", 9.2, 220), ("5.3", "gauss", 3, 256, 4, 4, "weak", 74, 1800),
+    ("5.3", "gauss", 3, 512, 4, 4, "weak", 590, 15000),
+    ("5.4", "slp", 3, 32, 4, 4, "strong", 2.1, 48), ("5.4", "slp", 3, 64, 4, 4, "strong", 23, 540),
+    ("5.4", "slp", 3, 128, 4, 4, "strong", 210, 5100),
+]
+
+
+def run_paper_tables(args):
+    """Construct (SHARED, FP64) and apply (one RHS) each setting of the paper's tables up to
+    --paper-max-n-points points; report GPU construction and matvec times beside the
+    paper's construction times, and the storage of the paper's layout (m_h) beside the
+    printed m_h.  Context only: the paper's code is MATLAB on one CPU socket."""
+    import torch
+    from paper_2508_05958_gb300 import htlr
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    rows = []
+    for (tab, kern, d, n, leaf, p, adm, mh, tc) in PAPER_ROWS:
+        N = n ** d
+        if N > args.paper_max_n_points:
+            continue
+        if kern == "gauss":
+            ktype, scale, param = 3, 1.0, math.sqrt(d)
+        else:
+            ktype, scale, param = (0, -1.0 / (2 * math.pi), 0.0) if d == 2 else (1, 1.0 / (4 * math.pi), 0.0)
+        eta = 0.0 if adm == "weak" else math.sqrt(d)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        H = htlr.htlr_construct(ktype, d, n, leaf, p, eta, kscale=scale, kparam=param,
+                                storage=2, stream=stream)
+        torch.cuda.synchronize()
+        t_con = time.perf_counter() - t0
+        info = htlr.htlr_info(H)
+        with torch.cuda.stream(stream):
+            u = torch.randn(1, N, dtype=torch.float64, device="cuda")
+            f = torch.empty_like(u)
+            for _ in range(3):
+                htlr.htlr_matvec(H, u, f, 1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(5):
+                htlr.htlr_matvec(H, u, f, 1)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        mv_ms = e0.elapsed_time(e1) / 5
+        htlr.htlr_free(H)
+        rows.append({"table": tab, "kernel": kern, "d": d, "N": N, "p": p, "admissibility": adm,
+                     "gpu_construct_s": t_con, "paper_tc_s": tc,
+                     "m_h_GiB": info["paper_storage_doubles"] * 8 / 2 ** 30, "paper_m_h_GB": mh,
+                     "held_GB": info["bytes_total"] / 1e9, "gpu_matvec_fp64_ms": mv_ms,
+                     "Gpts_per_s": N / (mv_ms * 1e-3) / 1e9})
+    print(json.dumps({"paper_tables": rows, "note": "paper times: MATLAB R2023b, one Xeon "
+                      "Gold 6226R (construction only; its matvec times are plots); GPU: "
+                      "SHARED storage, FP64, one RHS, CUDA events"}), flush=True)
+
+
 def main():
     args = parse()
+    if args.paper_tables:
+        run_paper_tables(args)
+        return
     from paper_2508_05958_gb300.workloads import workload
     w = workload(args.config)
     if args.impl == "reference":
