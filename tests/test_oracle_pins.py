@@ -430,3 +430,28 @@ def test_dense_tensor_grid_constant_kernel_weights(oracle):
     u = rng.standard_normal(n ** d)
     f = oracle.dense_rows(d, n, oracle.K_CONST, u, scale=2.0, grid=(x, e))
     assert np.allclose(f, 2.0 * (w @ u), rtol=0, atol=1e-13)
+
+
+def test_block_ranges_partition_the_product(oracle):
+    """The reference arm applies slices of the block list: the slices of any partition
+    add up to the whole HMultVec, there are as many blocks as far plus near blocks, and
+    the multiply-adds reported are p_eff^{2d} per far block and leaf^{2d} per near block."""
+    d, n, leaf, p = 3, 16, 4, 5
+    H = oracle.HTLR(d, n, 1, leaf, p, 1.0, a=np.linspace(0.5, 1.5, n ** d))
+    try:
+        far, near, _ = H.stats()
+        nb = H.nblocks()
+        assert nb == sum(far) + near
+        u = np.random.default_rng(3).standard_normal(n ** d)
+        whole = H.matvec(u)
+        f = np.zeros(n ** d)
+        cuts = [0, nb // 7, nb // 2, nb - 1, nb]
+        work = sum(H.matvec_range(u, f, a, b) for a, b in zip(cuts, cuts[1:]))
+        assert np.linalg.norm(f - whole) <= 1e-14 * np.linalg.norm(whole)
+        expect = near * float(leaf ** (2 * d))
+        for lv, c in enumerate(far):
+            pe = min(p, n >> lv)            # economy QR: p_eff = min(p, points per box side)
+            expect += c * float(pe ** (2 * d))
+        assert work == expect
+    finally:
+        H.free()
