@@ -395,3 +395,57 @@ def test_tensor_core_rejects_unsupported_mixes():
     with pytest.raises(htlr.HTLRError) as ei:
         htlr.htlr_construct(1, 3, 16, 4, 4, 1.0, storage=2, far_precision=0, near_precision=3)
     assert ei.value.code == htlr.HTLR_EUNSUPPORTED
+
+
+# ----------------------------------------------------------------------------------
+# Degenerate settings of the method
+# ----------------------------------------------------------------------------------
+@pytest.mark.parametrize("storage,far,near", [(1, 0, 0), (2, 1, 1), (2, 3, 3)])
+def test_nothing_admissible_is_the_dense_product(oracle, storage, far, near):
+    """eta so large that no block is admissible: the operator is its near field alone
+    and equals the dense Nystrom product (same diagonal rule) on every row."""
+    from paper_2508_05958_gb300.workloads import workload
+    w = workload("c2", n=16)
+    u = w.u(nrhs=3)
+    f, info = gpu_matvec(w, u, eta=1e6, storage=storage, far_precision=far, near_precision=near)
+    assert sum(info["far_per_level"]) == 0
+    assert info["near_blocks"] == (16 // 4) ** 6
+    fd = oracle.dense_rows(w.d, w.n, w.ktype, u, a=w.a())
+    assert rel(f, fd) < (TOL if near in (0, 1) else TC_TOL)
+
+
+def test_single_level_tree_2d(oracle):
+    """n = 2 leaf (one level below the root) with weak admissibility: four leaf boxes,
+    every pair of distinct boxes admissible at level 1, only the diagonal blocks dense."""
+    from paper_2508_05958_gb300.workloads import Workload
+    w = Workload("t1", d=2, n=16, ktype=3, leaf=8, p=6, eta=0.0, kparam=0.7, seed=5)
+    u = w.u(nrhs=2)
+    f, info = gpu_matvec(w, u)
+    assert info["far_per_level"] == [0, 12] and info["near_blocks"] == 4
+    ref, _ = _oracle_htlr(oracle, w, u)
+    assert rel(f, ref) < TOL
+
+
+def test_zero_and_constant_inputs():
+    """u = 0 gives f = 0 exactly; the constant kernel with a = 0 gives c h^d sum(u) in
+    every row (all blocks rank one), to rounding."""
+    import torch
+    from paper_2508_05958_gb300 import htlr
+    n, d = 16, 3
+    N = n ** d
+    H = htlr.htlr_construct(5, d, n, 4, 3, 1.0, kscale=2.5, storage=2)
+    try:
+        z = torch.zeros(2, N, dtype=torch.float64, device="cuda")
+        fz = torch.full_like(z, float("nan"))
+        htlr.htlr_matvec(H, z, fz)
+        htlr.htlr_sync(H)
+        assert torch.count_nonzero(fz).item() == 0
+        u = torch.from_numpy(np.random.default_rng(1).standard_normal((1, N))).cuda()
+        f = torch.empty_like(u)
+        htlr.htlr_matvec(H, u, f)
+        htlr.htlr_sync(H)
+        expect = 2.5 * (1.0 / n) ** d * u.sum().item()
+        # the diagonal entry of the constant kernel is its cell integral: c h^d as well
+        assert torch.allclose(f, torch.full_like(f, expect), rtol=0, atol=1e-12 * abs(expect) + 1e-14)
+    finally:
+        htlr.htlr_free(H)
