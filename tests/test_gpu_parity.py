@@ -402,12 +402,13 @@ def test_tensor_core_rejects_unsupported_mixes():
 # ----------------------------------------------------------------------------------
 @pytest.mark.parametrize("storage,far,near", [(1, 0, 0), (2, 1, 1), (2, 3, 3)])
 def test_nothing_admissible_is_the_dense_product(oracle, storage, far, near):
-    """eta so large that no block is admissible: the operator is its near field alone
-    and equals the dense Nystrom product (same diagonal rule) on every row."""
+    """eta so small that no block is admissible (Def. 2.3: max diam <= eta dist never
+    holds): the operator is its near field alone and equals the dense Nystrom product
+    (same diagonal rule) on every row."""
     from paper_2508_05958_gb300.workloads import workload
     w = workload("c2", n=16)
     u = w.u(nrhs=3)
-    f, info = gpu_matvec(w, u, eta=1e6, storage=storage, far_precision=far, near_precision=near)
+    f, info = gpu_matvec(w, u, eta=1e-9, storage=storage, far_precision=far, near_precision=near)
     assert sum(info["far_per_level"]) == 0
     assert info["near_blocks"] == (16 // 4) ** 6
     fd = oracle.dense_rows(w.d, w.n, w.ktype, u, a=w.a())
