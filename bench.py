@@ -50,6 +50,9 @@ def parse():
                     help="construct and apply the settings of the paper's Tables 5.1-5.4 "
                          "(context run; prints its own JSON line)")
     ap.add_argument("--paper-max-n-points", type=int, default=1 << 22)
+    ap.add_argument("--solve-large", action="store_true",
+                    help="16 second-kind GMRES solves on the c3 grid with a = 1 + 0.5 sin: "
+                         "FP64 against df64 residual + BF16X6 inner refinement")
     ap.add_argument("--autotune-ms", type=float, default=2000.0,
                     help="htlr_autotune budget before timing (0: keep the default shapes)")
     ap.add_argument("--serve-requests", type=int, default=120,
@@ -638,8 +641,45 @@ def run_paper_tables(args):
                       "SHARED storage, FP64, one RHS, CUDA events"}), flush=True)
 
 
+def run_solve_large(args):
+    """One batch of 16 GMRES(30) solves of a u + K u = f to 1e-10 on the c3 grid
+    (N = 2,097,152, 1/|x-y|, a = 1 + 0.5 sin 2 pi x_1): SHARED FP64 operator against the
+    df64 residual operator with a BF16X6 tensor-core inner operator (refinement)."""
+    import torch
+    from paper_2508_05958_gb300 import htlr
+    from paper_2508_05958_gb300.workloads import workload
+    torch.cuda.set_device(0)
+    w = workload("c3", a_kind="sin", nrhs=16)
+    stream = torch.cuda.Stream()
+    f = torch.from_numpy(np.ascontiguousarray(w.u(nrhs=16).T)).cuda()
+    out = {"workload": workload_desc(w, "SHARED"), "rhs": 16}
+    for name, acc, inner in (("mixed_refined_tensor_cores", (1, 1), (3, 3)), ("fp64", (0, 0), None)):
+        H = htlr.htlr_construct(w.ktype, w.d, w.n, w.leaf, w.p, w.eta, a=w.a(), storage=2,
+                                far_precision=acc[0], near_precision=acc[1], stream=stream)
+        Hi = None
+        if inner:
+            Hi = htlr.htlr_construct(w.ktype, w.d, w.n, w.leaf, w.p, w.eta, a=w.a(), storage=2,
+                                     far_precision=inner[0], near_precision=inner[1],
+                                     stream=stream)
+        u = torch.zeros_like(f)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = htlr.htlr_gmres(H, f, u, 16, H_inner=Hi, inner_tol=1e-5)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        out[name] = {"seconds": dt, "solves_per_s": 16 / dt, **res}
+        htlr.htlr_free(H)
+        if Hi:
+            htlr.htlr_free(Hi)
+    out["speedup"] = out["fp64"]["seconds"] / out["mixed_refined_tensor_cores"]["seconds"]
+    print(json.dumps({"solve_large": out}), flush=True)
+
+
 def main():
     args = parse()
+    if args.solve_large:
+        run_solve_large(args)
+        return
     if args.paper_tables:
         run_paper_tables(args)
         return
