@@ -36,7 +36,7 @@ typedef enum {
     HTLR_EINVAL = -1,        /* invalid argument (the message names it) */
     HTLR_ENOMEM = -2,        /* footprint above the HBM limit, checked before allocating */
     HTLR_ECUDA = -3,         /* a CUDA runtime call failed (message has the CUDA error) */
-    HTLR_EUNSUPPORTED = -4,  /* valid, but not supported by this build (e.g. SHARED storage
+    HTLR_EUNSUPPORTED = -4,  /* valid, but not supported by this library (e.g. SHARED storage
                                 on a non translation-invariant setting) */
     HTLR_ETIMEOUT = -5,      /* a bounded device wait ran out */
     HTLR_EDEVICE = -6        /* a kernel reported an internal check failure */

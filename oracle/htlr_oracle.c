@@ -22,7 +22,7 @@
  *   - a row-sampled HTLR product and dense product for large N
  *   - the block-tree counts and the paper's storage formula (Prop. 3.4/3.5, Tables 5.1-5.4)
  *
- * Readings where the paper is silent or garbled (also listed in the design doc):
+ * Readings where the paper is silent or garbled:
  *   - Lagrange basis: L_t(x) = prod_{j != t} (x - xi_j) / (xi_t - xi_j) (the printed
  *     formula swaps the indices; §3.1).
  *   - Admissibility is tested on the geometric tree cells [k 2^-l, (k+1) 2^-l]^d,
