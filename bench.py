@@ -50,6 +50,9 @@ def parse():
                     help="construct and apply the settings of the paper's Tables 5.1-5.4 "
                          "(context run; prints its own JSON line)")
     ap.add_argument("--paper-max-n-points", type=int, default=1 << 22)
+    ap.add_argument("--plan-compare", action="store_true",
+                    help="matvec time of htlr_matvec against a captured plan (CUDA graph) on "
+                         "c1 and c2")
     ap.add_argument("--solve-large", action="store_true",
                     help="16 second-kind GMRES solves on the c3 grid with a = 1 + 0.5 sin: "
                          "FP64 against df64 residual + BF16X6 inner refinement")
@@ -675,8 +678,49 @@ def run_solve_large(args):
     print(json.dumps({"solve_large": out}), flush=True)
 
 
+def run_plan_compare(args):
+    """Back-to-back matvecs (warm L2, CUDA events around 200 of them) issued one call at a
+    time with htlr_matvec, and replayed from a plan (one CUDA graph launch each)."""
+    import torch
+    from paper_2508_05958_gb300 import htlr
+    from paper_2508_05958_gb300.workloads import workload
+    torch.cuda.set_device(0)
+    out = []
+    for name, storage, prec in (("c1", 1, 0), ("c2", 2, 1), ("c2", 1, 1)):
+        w = workload(name)
+        stream = torch.cuda.Stream()
+        H = htlr.htlr_construct(w.ktype, w.d, w.n, w.leaf, w.p, w.eta, a=w.a(), storage=storage,
+                                far_precision=prec, near_precision=prec, stream=stream)
+        u = torch.from_numpy(np.ascontiguousarray(w.u(nrhs=1).T)).cuda()
+        f = torch.empty_like(u)
+        P = htlr.htlr_plan_create(H, u, f, 1)
+        res = {"workload": workload_desc(w, {1: "STORED", 2: "SHARED"}[storage] + " " +
+                                         PREC_NAME[prec]),
+               "launches_per_matvec": htlr.htlr_plan_launches(P)}
+        for mode in ("htlr_matvec", "plan"):
+            run = (lambda: htlr.htlr_matvec(H, u, f, 1)) if mode == "htlr_matvec" else \
+                  (lambda: htlr.htlr_plan_launch(P))
+            with torch.cuda.stream(stream):
+                for _ in range(20):
+                    run()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(200):
+                    run()
+                e1.record(stream)
+            torch.cuda.synchronize()
+            res[mode + "_us"] = e0.elapsed_time(e1) / 200 * 1e3
+        htlr.htlr_plan_free(P)
+        htlr.htlr_free(H)
+        out.append(res)
+    print(json.dumps({"plan_compare": out}), flush=True)
+
+
 def main():
     args = parse()
+    if args.plan_compare:
+        run_plan_compare(args)
+        return
     if args.solve_large:
         run_solve_large(args)
         return
