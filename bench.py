@@ -56,6 +56,11 @@ def parse():
     ap.add_argument("--solve-large", action="store_true",
                     help="16 second-kind GMRES solves on the c3 grid with a = 1 + 0.5 sin: "
                          "FP64 against df64 residual + BF16X6 inner refinement")
+    ap.add_argument("--accuracy", action="store_true",
+                    help="c3 and c4 at full size: error of every precision mode against the "
+                         "FP64 direct sums on seeded random rows, and the matvec time")
+    ap.add_argument("--accuracy-rows", type=int, default=1024)
+    ap.add_argument("--accuracy-configs", default="c3,c4")
     ap.add_argument("--autotune-ms", type=float, default=2000.0,
                     help="htlr_autotune budget before timing (0: keep the default shapes)")
     ap.add_argument("--serve-requests", type=int, default=120,
@@ -678,6 +683,88 @@ def run_solve_large(args):
     print(json.dumps({"solve_large": out}), flush=True)
 
 
+# precision modes (name, storage, far precision, near precision) of the accuracy run: the
+# plain FP64 path first, then the mixed ones; c4's tensor grid takes the generated near field
+ACCURACY_MODES = {
+    "c3": [("fp64", 2, 0, 0), ("df64", 2, 1, 1), ("f32 far / df64 near", 2, 2, 1),
+           ("bf16x6 far / df64 near", 2, 3, 1), ("bf16x6", 2, 3, 3)],
+    "c4": [("fp64", 3, 0, 0), ("bf16x6 far / f64 near", 3, 3, 0), ("f32", 3, 2, 2),
+           ("bf16x6 far / f32 near", 3, 3, 2)],
+}
+
+
+def _col_rel(f, ref):
+    """Per-column relative 2-norm errors over the sampled rows: (max, median)."""
+    e = np.linalg.norm(f - ref, axis=0) / np.linalg.norm(ref, axis=0)
+    return {"max": float(e.max()), "median": float(np.median(e))}
+
+
+def run_accuracy(args):
+    """Full-size error of every precision mode against the FP64 direct sums (the dense
+    Nystrom product, eq. (1.3)-(1.4)) on seeded random rows: c3 with its 64 RHS, c4 with
+    its 16.  The direct sums come from the CPU oracle (OpenMP, all host cores) before the
+    GPU is touched; each mode's matvec is timed with CUDA events (a single run for the
+    slow modes, the median of three after a warm-up for the fast ones)."""
+    import oracle
+    out = []
+    for name in [c for c in args.accuracy_configs.split(",") if c]:
+        from paper_2508_05958_gb300.workloads import workload
+        w = workload(name)
+        u = w.u(nrhs=w.nrhs)
+        rows = w.sample_rows(args.accuracy_rows, seed=1024)
+        t0 = time.perf_counter()
+        ref = oracle.dense_rows(w.d, w.n, w.ktype, u, rows, scale=w.kscale, param=w.kparam,
+                                grid=w.grid(), a=w.a(), q=w.q)
+        t_dense = time.perf_counter() - t0
+        out.append({"w": w, "u": u, "rows": rows, "ref": ref, "t_dense": t_dense})
+    import torch
+    from paper_2508_05958_gb300 import htlr
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    res_all = []
+    for item in out:
+        w, u, rows, ref = item["w"], item["u"], item["rows"], item["ref"]
+        ud = torch.from_numpy(np.ascontiguousarray(u.T)).cuda()
+        fd = torch.empty_like(ud)
+        rows_d = torch.from_numpy(rows).cuda()
+        res = {"workload": workload_desc(w, "").strip(), "rows": int(len(rows)),
+               "rhs": int(u.shape[1]), "direct_sums_s": item["t_dense"],
+               "direct_sums_cores": oracle.num_threads(), "modes": []}
+        f64 = None
+        for mname, storage, fp, np_ in ACCURACY_MODES.get(w.name, []):
+            H = htlr.htlr_construct(w.ktype, w.d, w.n, w.leaf, w.p, w.eta, kscale=w.kscale,
+                                    kparam=w.kparam, a=w.a(), grid=w.grid(), storage=storage,
+                                    stream=stream, far_precision=fp, near_precision=np_)
+            try:
+                info = htlr.htlr_info(H)
+                times = []
+                for k in range(4):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    htlr.htlr_matvec(H, ud, fd, u.shape[1])
+                    e1.record(stream)
+                    htlr.htlr_sync(H)
+                    times.append(e0.elapsed_time(e1))
+                    if times[0] > 2000.0:
+                        break
+                ms = times[0] if len(times) == 1 else statistics.median(times[1:])
+                with torch.cuda.stream(stream):
+                    fr = fd.index_select(1, rows_d).cpu().numpy().T.copy()
+            finally:
+                htlr.htlr_free(H)
+            m = {"mode": mname, "storage": {1: "STORED", 2: "SHARED", 3: "GENERATED"}[info["storage"]],
+                 "matvec_ms": ms, "rel_err_vs_direct_sums": _col_rel(fr, ref)}
+            if f64 is None:
+                f64 = fr
+            else:
+                m["rel_diff_vs_gpu_fp64"] = _col_rel(fr, f64)
+            res["modes"].append(m)
+            print(json.dumps({"accuracy_mode": w.name, **m}), flush=True)
+        res_all.append(res)
+    print(json.dumps({"accuracy": res_all}), flush=True)
+
+
 def run_plan_compare(args):
     """Back-to-back matvecs (warm L2, CUDA events around 200 of them) issued one call at a
     time with htlr_matvec, and replayed from a plan (one CUDA graph launch each)."""
@@ -718,6 +805,9 @@ def run_plan_compare(args):
 
 def main():
     args = parse()
+    if args.accuracy:
+        run_accuracy(args)
+        return
     if args.plan_compare:
         run_plan_compare(args)
         return

@@ -244,15 +244,28 @@ int orc_dense_rows(const orc_problem *P, const double *u, int nrhs, const int64_
             hi[l] = P->edge[l][mi[l] + 1];
         }
         double diag = orc_diag_integral(P, xi, lo, hi) + (P->a ? P->a[i] : 0.0);
-        for (int c = 0; c < nrhs; ++c) {
-            const double *uc = u + (long)c * N;
-            double s = 0.0;
-            for (long j = 0; j < N; ++j) {
-                if (j == i) continue;
-                s += orc_kernel(P, xi, xs + j * P->d) * w[j] * uc[j];
+        /* one kernel value per pair, used by every right-hand side: the values of a run
+         * of columns j are kept, then each right-hand side takes that run; every sum
+         * still runs over j in increasing order (j = i contributes through diag) */
+        enum { RUN = 4096 };
+        double *s = calloc((size_t)nrhs, sizeof(double));
+        double *kw = malloc(sizeof(double) * RUN);
+        for (long j0 = 0; j0 < N; j0 += RUN) {
+            const long j1 = j0 + RUN < N ? j0 + RUN : N;
+            for (long j = j0; j < j1; ++j)
+                kw[j - j0] = j == i ? 0.0 : orc_kernel(P, xi, xs + j * P->d) * w[j];
+            for (int c = 0; c < nrhs; ++c) {
+                const double *uc = u + (long)c * N;
+                double sc = s[c];
+                for (long j = j0; j < j1; ++j)
+                    if (j != i) sc += kw[j - j0] * uc[j];
+                s[c] = sc;
             }
-            frows[r + (long)c * nrows] = s + diag * uc[i];
         }
+        for (int c = 0; c < nrhs; ++c)
+            frows[r + (long)c * nrows] = s[c] + diag * u[(long)c * N + i];
+        free(kw);
+        free(s);
     }
     free(w);
     free(xs);
