@@ -95,7 +95,11 @@ typedef enum {
                             products formed with error-free FP32 transformations; results
                             within ~1e-14 of FP64.  Entries must lie within FP32 range,
                             |x| in [1e-30, 1e30], for that accuracy */
-    HTLR_PREC_FP32 = 2,  /* FP32 blocks, products and accumulation (~1e-7 relative) */
+    HTLR_PREC_FP32 = 2,  /* FP32 blocks, products and accumulation.  Unit roundoff 6e-8;
+                            measured 7e-9 to 1.5e-6 relative on the full-size operators,
+                            more where the result cancels (random u against a smooth
+                            kernel).  A generated near field sums each source leaf apart
+                            and then adds the leaf sums */
     HTLR_PREC_BF16X6 = 3 /* tensor cores (tcgen05): operands split into three BF16 terms,
                             the six products a_i b_j with i + j <= 4 (1-based) accumulated
                             in FP32 tensor memory; the many-right-hand-side path, 64 RHS at

@@ -86,6 +86,16 @@ __device__ __forceinline__ float ex2_approx(float x)
     return y;
 }
 
+// 1/sqrt(x) by the SFU (relative error near 2^-23).  x is a squared distance between
+// distinct points here, never subnormal; x = 0 (a point with itself) gives +inf, and the
+// sweep replaces that pair's value.
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Scale applied to the FP32 coordinates when they are staged, so that the exponential
 // kernels need no multiply per pair: exp(-r) = 2^(-r log2 e) with coordinates scaled by
 // log2 e, and exp(-r^2 / (2 sigma^2)) = 2^(-r^2) with coordinates scaled by
@@ -109,10 +119,10 @@ __device__ __forceinline__ T kv_eval(const KParams &k, int d, T r2, T dx0, T dx1
     if constexpr (KT == HTLR_K_LOG) {
         return (T)0.5 * log(r2);
     } else if constexpr (KT == HTLR_K_INV_R) {
-        if constexpr (sizeof(T) == 4) return rsqrtf(r2);
+        if constexpr (sizeof(T) == 4) return rsqrt_approx(r2);
         else return 1.0 / sqrt(r2);
     } else if constexpr (KT == HTLR_K_EXP_R) {
-        if constexpr (sizeof(T) == 4) return ex2_approx(-(r2 * rsqrtf(r2)));
+        if constexpr (sizeof(T) == 4) return ex2_approx(-(r2 * rsqrt_approx(r2)));
         else return exp(-sqrt(r2));
     } else if constexpr (KT == HTLR_K_GAUSS) {
         if constexpr (sizeof(T) == 4) return ex2_approx(-r2);
