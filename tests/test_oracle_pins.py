@@ -211,6 +211,34 @@ def test_dense_symmetry_and_rows(oracle):
     assert np.allclose(fr[:, 1], Av[rows], rtol=0, atol=1e-14)
 
 
+def test_dense_rows_many_columns_equal_the_written_out_sum(oracle):
+    """Rows of the Nystrom product (eq. (1.3)-(1.4)) for several right-hand sides at
+    N = 9216, beyond one 4096-column run of the oracle's loop: each column equals the
+    single-column call bit for bit, and the sum written out with numpy (kernel on the
+    grid, h^d weights, cell integral on the diagonal) to rounding."""
+    d, n = 2, 96
+    N, h = n ** d, 1.0 / n
+    rng = np.random.default_rng(21)
+    U = np.asfortranarray(rng.standard_normal((N, 3)))
+    a = rng.uniform(0.5, 1.5, N)
+    rows = np.array([0, 4095, 4096, 5000, N - 1])
+    fr = oracle.dense_rows(d, n, oracle.K_LOG, U, rows=rows, a=a)
+    for c in range(3):
+        one = oracle.dense_rows(d, n, oracle.K_LOG, np.ascontiguousarray(U[:, c]), rows=rows, a=a)
+        assert np.array_equal(one, fr[:, c])
+    g = (np.arange(n) + 0.5) * h
+    X = np.stack([np.tile(g, n), np.repeat(g, n)], axis=1)       # dim 1 fastest
+    for k, i in enumerate(rows):
+        r = np.linalg.norm(X - X[i], axis=1)
+        r[i] = 1.0
+        kv = np.log(r)
+        kv[i] = 0.0
+        lo = np.floor(X[i] / h) * h
+        diag = oracle.diag_integral(oracle.K_LOG, X[i], lo, lo + h)
+        expect = (kv * h ** d) @ U + (diag + a[i]) * U[i]
+        assert np.allclose(fr[k], expect, rtol=1e-13, atol=1e-13 * np.abs(expect).max())
+
+
 # ----------------------------------------------------------------------------------
 # Block cluster tree: the paper's printed storage (Tables 5.1-5.4) and closed counts
 # ----------------------------------------------------------------------------------
