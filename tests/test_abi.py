@@ -72,3 +72,31 @@ def test_null_and_dead_handles():
     assert L.htlr_last_launch_count(bogus) == -1
     k = htlr.htlr_kernel(1, 1.0, 0.0)
     assert L.htlr_construct(None, ctypes.byref(k), 3, 32, None, 4, 5, 1.0) == htlr.HTLR_EINVAL
+
+
+def test_product_and_oracle_share_no_code():
+    """The library and its binding never reach the CPU oracle, and the oracle includes
+    nothing of the library: the two are independent implementations."""
+    import glob
+    pkg = os.path.join(ROOT, "paper_2508_05958_gb300")
+    files = [p for ext in ("py", "cu", "cuh", "h") for p in
+             glob.glob(os.path.join(pkg, "**", "*." + ext), recursive=True)]
+    files += [os.path.join(ROOT, "include", "htlr.h")]
+    assert len(files) > 10
+    pat = re.compile(r"^\s*(import\s+oracle|from\s+oracle\b|from\s+\.\.\s*import\s+oracle)|"
+                     r"htlr_oracle|liboracle", re.M)
+    for p in files:
+        assert not pat.search(open(p).read()), p
+    src = open(os.path.join(ROOT, "oracle", "htlr_oracle.c")).read()
+    includes = re.findall(r'^\s*#\s*include\s*[<"]([^>"]+)[>"]', src, flags=re.M)
+    assert includes and all(not i.startswith("htlr") and "/" not in i for i in includes), includes
+
+
+def test_loading_the_library_does_not_import_the_oracle():
+    import subprocess
+    import sys
+    code = ("import sys; sys.path.insert(0, %r); import paper_2508_05958_gb300 as p; p.load(); "
+            "print('oracle' in sys.modules)" % ROOT)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd="/")
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == "False"
