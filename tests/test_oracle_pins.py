@@ -424,6 +424,26 @@ def test_paper_accuracy_band(oracle, row):
     assert ear / 10 < err < ear * 10, (err, ear)
 
 
+def test_htlr_tensor_grid_error_falls_at_the_interpolation_rate(oracle):
+    """Thm 3.2 on a quasi-uniform tensor grid (d = 3, n = 32, exp(-r), eta = 1): against
+    the direct sums the HTLR error falls geometrically in p, which pins the per-line
+    cell weights, the nodes on the geometric cells and the Kronecker order together."""
+    from paper_2508_05958_gb300.workloads import quasi_uniform_tensor_grid
+    d, n, leaf = 3, 32, 4
+    grid = quasi_uniform_tensor_grid(d, n, seed=9)
+    N = n ** d
+    u = np.random.default_rng(3).standard_normal(N)
+    rows = np.sort(np.random.default_rng(4).choice(N, 100, replace=False))
+    fd = oracle.dense_rows(d, n, oracle.K_EXP_R, u, rows=rows, grid=grid)
+    errs = []
+    for p in (2, 3, 4, 5):
+        fh = oracle.htlr_rows(d, n, oracle.K_EXP_R, leaf, p, 1.0, u, rows, grid=grid,
+                              orth=False)
+        errs.append(np.linalg.norm(fh - fd) / np.linalg.norm(fd))
+    assert all(b < a / 8 for a, b in zip(errs, errs[1:])), errs
+    assert errs[-1] < 2e-6, errs
+
+
 @pytest.mark.parametrize("d,n,leaf,p,eta", [(2, 32, 4, 4, 1.0), (3, 16, 4, 3, 1.0),
                                             (3, 16, 4, 3, 0.0)])
 def test_htlr_polynomial_kernel_exact_on_tensor_grid(oracle, d, n, leaf, p, eta):
