@@ -61,6 +61,11 @@ def parse():
                          "FP64 direct sums on seeded random rows, and the matvec time")
     ap.add_argument("--accuracy-rows", type=int, default=1024)
     ap.add_argument("--accuracy-configs", default="c3,c4")
+    ap.add_argument("--accuracy-modes", default="",
+                    help="comma list of mode names to run (default: all of the workload's)")
+    ap.add_argument("--accuracy-tc-segments", default="",
+                    help="comma list of tc_segment values: each BF16X6 mode also runs with "
+                         "each of them")
     ap.add_argument("--autotune-ms", type=float, default=2000.0,
                     help="htlr_autotune budget before timing (0: keep the default shapes)")
     ap.add_argument("--serve-requests", type=int, default=120,
@@ -731,10 +736,18 @@ def run_accuracy(args):
                "rhs": int(u.shape[1]), "direct_sums_s": item["t_dense"],
                "direct_sums_cores": oracle.num_threads(), "modes": []}
         f64 = None
-        for mname, storage, fp, np_ in ACCURACY_MODES.get(w.name, []):
+        modes = [(m, st, fp, np_, 0) for m, st, fp, np_ in ACCURACY_MODES.get(w.name, [])]
+        if args.accuracy_modes:
+            keep = set(args.accuracy_modes.split(","))
+            modes = [m for m in modes if m[0] in keep]
+        segs = [int(v) for v in args.accuracy_tc_segments.split(",") if v]
+        modes += [(f"{m} (tc_segment {sg})", st, fp, np_, sg) for m, st, fp, np_, _ in modes
+                  if fp == 3 for sg in segs]
+        for mname, storage, fp, np_, seg in modes:
             H = htlr.htlr_construct(w.ktype, w.d, w.n, w.leaf, w.p, w.eta, kscale=w.kscale,
                                     kparam=w.kparam, a=w.a(), grid=w.grid(), storage=storage,
-                                    stream=stream, far_precision=fp, near_precision=np_)
+                                    stream=stream, far_precision=fp, near_precision=np_,
+                                    tc_segment=seg)
             try:
                 info = htlr.htlr_info(H)
                 times = []
@@ -755,9 +768,9 @@ def run_accuracy(args):
                 htlr.htlr_free(H)
             m = {"mode": mname, "storage": {1: "STORED", 2: "SHARED", 3: "GENERATED"}[info["storage"]],
                  "matvec_ms": ms, "rel_err_vs_direct_sums": _col_rel(fr, ref)}
-            if f64 is None:
+            if mname == "fp64":
                 f64 = fr
-            else:
+            elif f64 is not None:
                 m["rel_diff_vs_gpu_fp64"] = _col_rel(fr, f64)
             res["modes"].append(m)
             print(json.dumps({"accuracy_mode": w.name, **m}), flush=True)
