@@ -73,6 +73,16 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-max-n2", type=int, default=512)
     ap.add_argument("--serve-max-n3", type=int, default=64)
+    ap.add_argument("--workloads", default="c2_fp64,c3,c4",
+                    help="comma list of extra workloads measured after the headline and "
+                         "reported under 'workloads' (empty: none)")
+    ap.add_argument("--workload-steps", type=int, default=5,
+                    help="timed matvecs of each extra workload")
+    ap.add_argument("--workload-rows", type=int, default=1024,
+                    help="seeded random rows of the FP64 direct sums per extra workload")
+    ap.add_argument("--workload-oracle-rows", type=int, default=8,
+                    help="rows of the oracle's row-sampled HTLR per extra workload (parity "
+                         "and the CPU baseline)")
     return ap.parse_args()
 
 
@@ -178,9 +188,11 @@ class ClockSampler:
 # CPU oracle timing (reference arm and cpu_baseline leg)
 # ----------------------------------------------------------------------------------
 def time_oracle(w, budget_s):
-    """Times the oracle's HMultVec (Algorithm 2, block by block) on this workload after its
-    construction.  Returns (Gpts*RHS/s, cores, sample description, seconds)."""
+    """Times the oracle's HMultVec (Algorithm 2, every block's product on all host cores,
+    results added in recursion order) on this workload after its construction.  Returns
+    (Gpts*RHS/s, cores, sample description, seconds)."""
     import oracle
+    cores = oracle.set_num_threads(0)
     t0 = time.perf_counter()
     H = oracle.HTLR(w.d, w.n, w.ktype, w.leaf, w.p, w.eta, a=w.a(), scale=w.kscale, **oracle_args(w),
                     param=w.kparam)
@@ -198,59 +210,46 @@ def time_oracle(w, budget_s):
     time_oracle.last_output = np.asarray(f_ref).reshape(-1)
     t = statistics.median(times)
     val = w.N * 1 / t / 1e9
-    sample = (f"oracle construct {t_con:.1f} s (OpenMP, {oracle.num_threads()} threads) then "
-              f"{len(times)} single-threaded HMultVec calls on the full workload, 1 RHS, "
-              f"median {t * 1e3:.1f} ms")
-    return val, 1, sample, t
+    sample = (f"oracle construct {t_con:.1f} s, then {len(times)} HMultVec calls on the full "
+              f"workload, 1 RHS, {cores} OpenMP threads (host cores), median {t * 1e3:.1f} ms")
+    return val, cores, sample, t
 
 
 def run_reference(args, w):
+    """The reference arm: the oracle's HMultVec (Algorithm 2 on every block, all host
+    cores) on the same workload; each step is one whole product."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     import oracle
     oracle.build()
     import oracle as O
+    cores = O.set_num_threads(0)
     t0 = time.perf_counter()
     H = O.HTLR(w.d, w.n, w.ktype, w.leaf, w.p, w.eta, a=w.a(), scale=w.kscale, param=w.kparam,
                **oracle_args(w))
     t_con = time.perf_counter() - t0
-    u = np.ascontiguousarray(w.u(nrhs=1)[:, 0])
-    f = np.zeros(w.N)
-    nblk = H.nblocks()
-    # one full HMultVec gives the total work and the time per unit of work; each step is
-    # then a bounded slice of the block list (recursion order, wrapping around), sized so
-    # that the K + W steps take about `--cpu-sample-s` seconds (at least one block)
-    t1 = time.perf_counter()
-    total_work = H.matvec_range(u, f, 0, nblk)
-    t_full = time.perf_counter() - t1
-    per_step_s = max(1e-3, args.cpu_sample_s / max(1, args.steps + args.warmup))
-    slice_blocks = int(min(nblk, max(1, nblk * per_step_s / max(t_full, 1e-9))))
-    k0 = 0
+    u = w.u(nrhs=w.nrhs)
+    nrhs = u.shape[1]
     for _ in range(args.warmup):
-        H.matvec_range(u, f, k0, k0 + slice_blocks)
-        k0 = (k0 + slice_blocks) % nblk
-    times, works = [], []
+        H.matvec(u)
+    times = []
     for _ in range(args.steps):
         t1 = time.perf_counter()
-        wk = H.matvec_range(u, f, k0, min(nblk, k0 + slice_blocks))
+        H.matvec(u)
         times.append(time.perf_counter() - t1)
-        works.append(wk)
-        k0 = (k0 + slice_blocks) % nblk
     H.free()
-    # points * RHS per second: the slice's share of the product's work times N
     t = statistics.mean(times)
-    val = sum(w.N * wk / total_work for wk in works) / sum(times) / 1e9
+    val = w.N * nrhs / t / 1e9
     line = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": workload_desc(w, "oracle (per-block)")},
-        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"construct {t_con:.1f} s once (OpenMP); one full HMultVec "
-                                   f"({t_full:.2f} s) for the work total; then each step applies "
-                                   f"{slice_blocks} of the {nblk} blocks (Algorithm 2, one "
-                                   f"thread), credited with its share of the work x N points"},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"construct {t_con:.1f} s once; each step one whole "
+                                   f"HMultVec (Algorithm 2, every block, {nrhs} RHS) on "
+                                   f"{cores} OpenMP threads"},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
     }
@@ -363,6 +362,173 @@ def near_cc_roofline(info, w, nrhs, ms):
     if generated:
         roof["kernel_evaluations_per_s"] = pairs / t
     return roof
+
+
+# Extra workloads measured after the headline (name, storage, far and near precision).
+SUITE = {
+    "c2_fp64": ("c2", 1, 0, 0),     # the headline operator in plain FP64 (STORED)
+    "c3": ("c3", 2, 3, 3),          # 64 RHS, SHARED, BF16x6 tensor cores far and near
+    "c4": ("c4", 3, 3, 2),          # 16 RHS, tensor grid: BF16x6 far, FP32 generated near
+}
+
+# DRAM traffic per executed BF16 tensor FLOP of the grouped tensor-core kernel (all its
+# launches of one matvec), from ncu on the n = 64 profiling cases of the same operators
+# and kernel build (profiles/); the full-size traffic is this ratio times the executed
+# FLOPs of the full-size matvec, since every launch streams its cores and sources per
+# group and offset.  None: not captured for the current kernel.
+TRAFFIC_PER_TENSOR_FLOP = {"c3": None, "c4": None}
+
+
+def tensor_roofline(info, w, nrhs, stream_ms, bf16_peak, executed_flops):
+    """Roofline of the tensor-core stream stage (all grouped launches of one matvec, with
+    their operand packing): algorithmic work = the method's multiply-adds (every far core
+    p_eff^2d and tensor-core near block |tau||sigma|, per RHS) x 6 split products x 2
+    FLOPs, against the measured BF16 peak; the executed fraction (MMA padding included)
+    is given beside it."""
+    far, near, _, _ = stream_elements(info, w)
+    macs = (far + (near if info["near_precision"] == 3 else 0.0)) * nrhs
+    t = stream_ms * 1e-3
+    alg = 2.0 * 6.0 * macs
+    roof = {"bound": "tensor", "achieved": alg / t / 1e12, "peak": bf16_peak, "unit": "TFLOP/s",
+            "frac": alg / t / 1e12 / bf16_peak,
+            "peak_source": "measured bf16 burst (MEASURED_PEAKS.json)",
+            "kernel": "tc_group_kernel (tcgen05 kind::f16, BF16x6; stage includes operand packing)",
+            "kernel_ms": stream_ms, "multiply_adds_per_launch": macs,
+            "algorithmic_bf16_flops_per_launch": alg,
+            "executed_bf16_flops_per_launch": executed_flops,
+            "executed_frac": executed_flops / t / 1e12 / bf16_peak, "traffic": None}
+    ratio = TRAFFIC_PER_TENSOR_FLOP.get(w.name)
+    if ratio:
+        roof["traffic"] = ratio * executed_flops
+        roof["traffic_source"] = ("ncu dram bytes per executed tensor FLOP on the n=64 case x "
+                                  "executed FLOPs here")
+    return roof
+
+
+def run_suite_workload(key, args, stream, peaks, hbm_peak, hbm_src):
+    """One extra workload: construct, time `--workload-steps` matvecs (CUDA events on the
+    handle's stream), stage times, roofline, error against the FP64 direct sums on seeded
+    random rows, parity against the oracle's row-sampled HTLR, and the CPU baseline from
+    that oracle's timing."""
+    import torch
+    import oracle
+    from paper_2508_05958_gb300 import htlr
+    from paper_2508_05958_gb300.workloads import workload
+    name, storage, fp, np_ = SUITE[key]
+    w = workload(name)
+    nrhs = w.nrhs
+    U = w.u(nrhs=nrhs)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    H = htlr.htlr_construct(w.ktype, w.d, w.n, w.leaf, w.p, w.eta, kscale=w.kscale,
+                            kparam=w.kparam, a=w.a(), grid=w.grid(), storage=storage,
+                            stream=stream, far_precision=fp, near_precision=np_)
+    torch.cuda.synchronize()
+    construct_s = time.perf_counter() - t0
+    out = {}
+    try:
+        if name == "c2":
+            htlr.htlr_autotune(H, nrhs=nrhs, budget_ms=1000.0)
+        info = htlr.htlr_info(H)
+        storage_name = ({1: "STORED", 2: "SHARED", 3: "GENERATED"}[info["storage"]] + " " +
+                        dtype_name(info))
+        with torch.cuda.stream(stream):
+            ud = torch.from_numpy(np.ascontiguousarray(U.T)).cuda()
+            fd = torch.empty_like(ud)
+            flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        for _ in range(2):
+            htlr.htlr_matvec(H, ud, fd, nrhs)
+        htlr.htlr_sync(H)
+        steps = args.workload_steps if name != "c2" else max(args.workload_steps, 20)
+        clocks = ClockSampler(torch.cuda.current_device())
+        clocks.start()
+        time.sleep(0.3)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            for k in range(steps):
+                flush.fill_(float(k))             # evicts L2 (256 MB > 129 MB)
+                ev[k][0].record(stream)
+                htlr.htlr_matvec(H, ud, fd, nrhs)
+                ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        htlr.htlr_sync(H)                         # a device check that failed voids the line
+        launches = htlr.htlr_last_launch_count(H) * steps
+        ms = [a.elapsed_time(b) for a, b in ev]
+        mean_ms = float(np.mean(ms))
+        stage = np.zeros(5)
+        nst = 3 if name != "c2" else 10
+        for k in range(nst):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(k))
+            stage += np.array(htlr.htlr_matvec_timed(H, ud, fd, nrhs))
+        stage_ms = stage / nst
+        roofs = []
+        if fp == 3:
+            roofs.append(tensor_roofline(info, w, nrhs, stage_ms[1], peaks.get("bf16_tflops", 1885.6),
+                                         htlr.htlr_tensor_flops(H, nrhs)))
+        else:
+            roofs.append(stream_roofline(info, w, nrhs, stage_ms[1], hbm_peak, hbm_src))
+        if stage_ms[2] > 1e-2:
+            roofs.append(near_cc_roofline(info, w, nrhs, stage_ms[2]))
+        roofs.sort(key=lambda r: -r["kernel_ms"])
+        # the timed product's rows (the last timed matvec left f in fd)
+        rows = w.sample_rows(args.workload_rows, seed=1024) if w.N > 100000 else None
+        with torch.cuda.stream(stream):
+            f_all = fd.cpu().numpy().T
+        torch.cuda.synchronize()
+        out = {
+            "workload": workload_desc(w, storage_name), "nrhs": nrhs,
+            "value": w.N * nrhs / (mean_ms * 1e-3) / 1e9, "unit": UNIT,
+            "matvec_ms": {"mean": mean_ms, "median": float(np.median(ms)), "min": float(min(ms)),
+                          "steps": steps},
+            "l2": ("flushed between steps (256 MB write)" if w.N * nrhs * 8 < 129e6 else
+                   "u and f (%.2f GB each) exceed L2; flushed between steps as well" %
+                   (w.N * nrhs * 8 / 1e9)),
+            "construct_s": construct_s,
+            "stage_ms": {"up": stage_ms[0], "stream": stage_ms[1], "near_cuda_cores": stage_ms[2],
+                         "reduce": stage_ms[3], "out": stage_ms[4]},
+            "roofline": roofs[0], "roofline_other": roofs[1:], "clocks": clk,
+            "gpu_launches": launches, "bytes_held": info["bytes_total"],
+        }
+    finally:
+        htlr.htlr_free(H)
+    # ---- CPU side: parity and accuracy on sampled rows, and the oracle's timing ----
+    cores = oracle.set_num_threads(0)
+    okw = oracle_args(w)
+    if rows is None:
+        # small operator: the whole oracle HTLR (every row) and its HMultVec time
+        val, cores, sample, t = time_oracle(w, min(args.cpu_sample_s, 5.0))
+        ref = time_oracle.last_output
+        out["parity_vs_oracle_htlr"] = {"rel_err": float(np.linalg.norm(f_all[:, 0] - ref) /
+                                                         np.linalg.norm(ref)),
+                                        "tolerance": 1e-12, "compared": "RHS 1, all N rows"}
+        out["cpu_baseline"] = {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": sample}
+        return out
+    t0 = time.perf_counter()
+    ref = oracle.dense_rows(w.d, w.n, w.ktype, U, rows, scale=w.kscale, param=w.kparam,
+                            grid=w.grid(), a=w.a(), q=w.q)
+    t_dense = time.perf_counter() - t0
+    out["error_vs_direct_sums"] = dict(_col_rel(f_all[rows], ref), rows=int(len(rows)),
+                                       rhs=nrhs, direct_sums_s=t_dense, cores=cores)
+    orows = w.sample_rows(args.workload_oracle_rows, seed=4096)
+    t0 = time.perf_counter()
+    oref = oracle.htlr_rows(w.d, w.n, w.ktype, w.leaf, w.p, w.eta, U, orows, scale=w.kscale,
+                            param=w.kparam, a=w.a(), **okw)
+    t_rows = time.perf_counter() - t0
+    out["parity_vs_oracle_htlr"] = dict(_col_rel(f_all[orows], oref), rows=int(len(orows)),
+                                        rhs=nrhs)
+    out["cpu_baseline"] = {"value": len(orows) * nrhs / t_rows / 1e9, "unit": UNIT,
+                           "cores": cores, "kind": "oracle",
+                           "sample": f"row-sampled oracle HTLR (Algorithms 1-2 on every block "
+                                     f"of the sampled rows' target boxes): {len(orows)} rows x "
+                                     f"{nrhs} RHS in {t_rows:.1f} s on {cores} OpenMP threads; "
+                                     f"rows x RHS per second, extrapolated per row"}
+    return out
 
 
 def time_gmres(w, solves, stream):
@@ -508,6 +674,9 @@ def run_gpu(args, w):
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
+    # a device check that failed inside the timed region (a bounded wait that ran out)
+    # voids the measurement: htlr_sync raises and no line is printed
+    htlr.htlr_sync(H)
     step_ms = [a.elapsed_time(b) for a, b in ev]
     ms = max_over_ranks(float(np.mean(step_ms)), world, "cuda")
     value = replica_throughput(world, w.N, nrhs, ms)
@@ -564,12 +733,16 @@ def run_gpu(args, w):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
     }
+    f_head = fd[0].double().cpu().numpy()             # first RHS of the last timed matvec
+    if world == 1 and args.workloads:
+        line["workloads"] = {k: run_suite_workload(k, args, stream, peaks, hbm_peak, hbm_src)
+                             for k in args.workloads.split(",") if k}
     if args.gmres_solves > 0 and w.a_kind != "zero":
         line["gmres"] = time_gmres(w, args.gmres_solves, stream)
     if args.serve_requests > 0 and world == 1:
         line["serving"] = time_serving(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        f_gpu = fd[0].double().cpu().numpy()          # first RHS of the last timed matvec
+        f_gpu = f_head
         val, cores, sample, _ = time_oracle(w, args.cpu_sample_s)
         f_ref = time_oracle.last_output
         tol = {0: 1e-12, 1: 1e-12, 2: 1e-6, 3: 1e-3}[max(info["far_precision"],

@@ -131,6 +131,13 @@ typedef struct {
                             (0: default 8).  The FP32 accumulation of the tensor cores loses
                             about 2^-25 relative per MMA, so shorter segments are more
                             accurate and drain more often */
+    long long tc_wait_cycles; /* limit, in SM clock cycles, of every bounded wait inside the
+                            tensor-core kernels (a copy, an MMA or a drain that does not
+                            complete): 0 selects the default 4e9 (about 2 s at 2 GHz).  When
+                            a wait runs out the kernel stops its work, lets what it already
+                            issued complete, releases its tensor memory and returns; the
+                            matvec's result is then invalid and htlr_sync (or the next
+                            synchronous call) returns HTLR_ETIMEOUT */
 } htlr_options;
 
 /* Statistics of a constructed operator (htlr_info). */
@@ -412,8 +419,24 @@ int htlr_info(const htlr_handle *H, htlr_stats *s);
 /* Replace the stream used by later calls on H (NULL: default stream). */
 int htlr_set_stream(htlr_handle *H, void *stream);
 
-/* Wait for the handle's stream and report any device-side check failure (HTLR_EDEVICE). */
+/*
+ * htlr_sync -- wait for the handle's stream, then read and clear the handle's device error
+ * word.  Returns HTLR_ETIMEOUT when a bounded wait of a tensor-core kernel ran out in any
+ * work enqueued since the word was last read (those matvecs' results are invalid),
+ * HTLR_EDEVICE for any other device-side check, HTLR_OK otherwise.  The word is cleared
+ * when it is reported, so each failure is reported once and the handle stays usable.
+ * The synchronous entry points (htlr_matvec_host, htlr_matvec_timed, htlr_gmres) read it
+ * the same way before they return; htlr_matvec and htlr_plan_launch are asynchronous
+ * and leave it to htlr_sync.
+ */
 int htlr_sync(const htlr_handle *H);
+
+/*
+ * htlr_set_wait_limit -- replace the handle's bounded-wait limit (htlr_options
+ * tc_wait_cycles; 0 restores the default) for later matvecs.  Plans captured on H
+ * re-capture on their next launch.  HTLR_EINVAL for a negative limit.
+ */
+int htlr_set_wait_limit(htlr_handle *H, long long cycles);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char *htlr_last_error(void);

@@ -101,6 +101,8 @@ def lib():
             L.orc_htlr_nblocks.argtypes = [ctypes.c_void_p]
             L.orc_num_threads.restype = ctypes.c_int
             L.orc_num_threads.argtypes = []
+            L.orc_set_num_threads.restype = ctypes.c_int
+            L.orc_set_num_threads.argtypes = [ctypes.c_int]
             _lib = L
     return _lib
 
@@ -173,6 +175,12 @@ def qr(A):
 
 def num_threads():
     return lib().orc_num_threads()
+
+
+def set_num_threads(n):
+    """Threads of the oracle's OpenMP loops (n <= 0 keeps the current count); returns the
+    count in effect."""
+    return lib().orc_set_num_threads(int(n))
 
 
 # ----------------------------------------------------------------------------------

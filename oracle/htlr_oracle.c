@@ -891,8 +891,9 @@ static void scatter_add_box(const orc_problem *P, const orc_box *B, const double
     }
 }
 
-/* f_tau += A_{tau,sigma} u_sigma for one block (the two leaf cases of Algorithm 2). */
-static void apply_block(const orc_problem *P, const orc_block *K, const double *u, double *f)
+/* v = A_{tau,sigma} u_sigma for one block (the two leaf cases of Algorithm 2); v has
+ * |tau| entries in the box's local order (first index fastest). */
+static void block_product(const orc_problem *P, const orc_block *K, const double *u, double *v)
 {
     int d = P->d;
     const orc_box *t = &K->tau, *s = &K->sig;
@@ -937,31 +938,146 @@ static void apply_block(const orc_problem *P, const orc_block *K, const double *
             F = F2;
             memcpy(dims, od, sizeof od);
         }
-        scatter_add_box(P, t, F, f);
+        memcpy(v, F, sizeof(double) * nt);
         free(F);
     } else {
-        double *v = calloc(nt, sizeof(double));
+        for (long it = 0; it < nt; ++it) v[it] = 0.0;
         for (long js = 0; js < ns; ++js)
             for (long it = 0; it < nt; ++it) v[it] += K->D[it + nt * js] * us[js];
-        scatter_add_box(P, t, v, f);
-        free(v);
         free(us);
     }
 }
 
+/* f_tau += A_{tau,sigma} u_sigma for one block. */
+static void apply_block(const orc_problem *P, const orc_block *K, const double *u, double *f)
+{
+    long nt = 1;
+    for (int l = 0; l < P->d; ++l) nt *= K->tau.cnt[l];
+    double *v = malloc(sizeof(double) * nt);
+    block_product(P, K, u, v);
+    scatter_add_box(P, &K->tau, v, f);
+    free(v);
+}
+
 /* HMultVec (Algorithm 2) from the root: f = A u (f starts at zero), column by column.
- * The blocks are visited in the order of the block-tree recursion. */
+ * The blocks are visited in the order of the block-tree recursion.  Serially that is
+ * f_tau += A_{tau,sigma} u_sigma block after block.  Here the per-block products run on
+ * all host cores (OpenMP), each into its own buffer; then every leaf box of the tree
+ * gathers, in recursion order, the contributions of the blocks whose target box
+ * contains it.  Each element of f thus receives the same additions in the same order as
+ * in the serial loop, and the result is bitwise independent of the thread count. */
 int orc_htlr_matvec(const orc_htlr *H, const double *u, int nrhs, double *f)
 {
+    const orc_problem *P = &H->P;
+    const int d = P->d, L = H->L;
     long N = 1;
-    for (int l = 0; l < H->P.d; ++l) N *= H->P.n;
+    for (int l = 0; l < d; ++l) N *= P->n;
+    const long nblk = H->nblk;
+    long *off = malloc(sizeof(long) * (nblk + 1));
+    off[0] = 0;
+    for (long k = 0; k < nblk; ++k) {
+        long nt = 1;
+        for (int l = 0; l < d; ++l) nt *= H->blk[k].tau.cnt[l];
+        off[k + 1] = off[k] + nt;
+    }
+    double *buf = malloc(sizeof(double) * (off[nblk] > 0 ? off[nblk] : 1));
+    /* per leaf box: the blocks whose target box contains it, in recursion order */
+    const int nl1 = 1 << L;
+    long nleaf = 1;
+    for (int l = 0; l < d; ++l) nleaf *= nl1;
+    long *lcnt = calloc(nleaf + 1, sizeof(long));
+    for (long k = 0; k < nblk; ++k) {
+        const orc_box *t = &H->blk[k].tau;
+        const int sh = L - t->level, w = 1 << sh;
+        long span = 1;
+        for (int l = 0; l < d; ++l) span *= w;
+        for (long q = 0; q < span; ++q) {
+            long rem = q, leaf = 0, str = 1;
+            for (int l = 0; l < d; ++l) {
+                leaf += (long)((t->b[l] << sh) + rem % w) * str;
+                rem /= w;
+                str *= nl1;
+            }
+            lcnt[leaf + 1]++;
+        }
+    }
+    for (long b = 0; b < nleaf; ++b) lcnt[b + 1] += lcnt[b];
+    long *lblk = malloc(sizeof(long) * (lcnt[nleaf] > 0 ? lcnt[nleaf] : 1));
+    long *fill = malloc(sizeof(long) * (nleaf > 0 ? nleaf : 1));
+    for (long b = 0; b < nleaf; ++b) fill[b] = lcnt[b];
+    for (long k = 0; k < nblk; ++k) {          /* increasing k: lists in recursion order */
+        const orc_box *t = &H->blk[k].tau;
+        const int sh = L - t->level, w = 1 << sh;
+        long span = 1;
+        for (int l = 0; l < d; ++l) span *= w;
+        for (long q = 0; q < span; ++q) {
+            long rem = q, leaf = 0, str = 1;
+            for (int l = 0; l < d; ++l) {
+                leaf += (long)((t->b[l] << sh) + rem % w) * str;
+                rem /= w;
+                str *= nl1;
+            }
+            lblk[fill[leaf]++] = k;
+        }
+    }
+    free(fill);
     for (int c = 0; c < nrhs; ++c) {
         const double *uc = u + (long)c * N;
         double *fc = f + (long)c * N;
         memset(fc, 0, sizeof(double) * N);
-        for (long k = 0; k < H->nblk; ++k) apply_block(&H->P, &H->blk[k], uc, fc);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+        for (long k = 0; k < nblk; ++k) block_product(P, &H->blk[k], uc, buf + off[k]);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+        for (long b = 0; b < nleaf; ++b) {
+            int bl[3] = {0, 0, 0};
+            long rem = b;
+            for (int l = 0; l < d; ++l) { bl[l] = (int)(rem % nl1); rem /= nl1; }
+            orc_box lf;
+            make_box(P, L, bl, &lf);
+            for (long e = lcnt[b]; e < lcnt[b + 1]; ++e) {
+                const long k = lblk[e];
+                const orc_box *t = &H->blk[k].tau;
+                const double *v = buf + off[k];
+                /* every point of the leaf: its index in the target box and in f */
+                for (int i3 = 0; i3 < lf.cnt[2]; ++i3)
+                    for (int i2 = 0; i2 < lf.cnt[1]; ++i2)
+                        for (int i1 = 0; i1 < lf.cnt[0]; ++i1) {
+                            const int gi[3] = {lf.first[0] + i1, lf.first[1] + i2,
+                                               lf.first[2] + i3};
+                            long g = 0, gs = 1, j = 0, js = 1;
+                            for (int l = 0; l < d; ++l) {
+                                g += gi[l] * gs;
+                                gs *= P->n;
+                                j += (gi[l] - t->first[l]) * js;
+                                js *= t->cnt[l];
+                            }
+                            fc[g] += v[j];
+                        }
+            }
+        }
     }
+    free(lblk);
+    free(lcnt);
+    free(buf);
+    free(off);
     return 0;
+}
+
+/* Thread count of the oracle's OpenMP loops (n <= 0: the OpenMP default).  Returns the
+ * count now in effect. */
+int orc_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }
 
 /* ------------------------------------------------------------------------------ */

@@ -38,7 +38,8 @@ def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = sources() + glob.glob(os.path.join(SRC_DIR, "*.h")) + [os.path.join(INCLUDE, "htlr.h")]
+    deps = (sources() + glob.glob(os.path.join(SRC_DIR, "*.h")) +
+            glob.glob(os.path.join(SRC_DIR, "*.cuh")) + [os.path.join(INCLUDE, "htlr.h")])
     return any(os.path.getmtime(p) > t for p in deps)
 
 

@@ -365,6 +365,12 @@ extern "C" int htlr_gmres(const htlr_handle *H, const htlr_handle *H_inner, cons
     }
     e = cudaStreamSynchronize(H->stream);
     if (e != cudaSuccess) return cuda_fail(e, "htlr_gmres");
+    if (H_inner && (e = cudaStreamSynchronize(H_inner->stream)) != cudaSuccess)
+        return cuda_fail(e, "htlr_gmres");
+    // a device check that failed in any matvec of the solve (a bounded wait that ran out)
+    // invalidates the result
+    if ((rc = check_device_error(H, "htlr_gmres"))) return rc;
+    if (H_inner && (rc = check_device_error(H_inner, "htlr_gmres (inner operator)"))) return rc;
     if (res) {
         res->iterations = iters;
         res->matvecs = matvecs;

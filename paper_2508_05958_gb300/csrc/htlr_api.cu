@@ -1296,6 +1296,7 @@ int run_chunk(const htlr_handle *H, const KindDesc *d_kinds, double *part,
             a.tmem_cols = cols;
             a.part = H->d_part_tc;
             a.err = H->d_err;
+            a.wait_cycles = H->tc_wait_cycles;
             launch_tc_stream(a, s);
         };
         // grouped path: G = 128 / Rpg targets per MMA
@@ -1339,6 +1340,7 @@ int run_chunk(const htlr_handle *H, const KindDesc *d_kinds, double *part,
             while (cols < 2 * tg.Nw) cols *= 2;   // two accumulator buffers
             g.tmem_cols = cols;
             g.err = H->d_err;
+            g.wait_cycles = H->tc_wait_cycles;
             launch_tc_group(g, tm.b, s);
         };
         for (int lv = 1; lv <= L; ++lv) {
@@ -1487,6 +1489,28 @@ static int enqueue_matvec(const htlr_handle *H, const double *u, double *f, int 
     return HTLR_OK;
 }
 
+// Reads the handle's device error word after its stream has drained, clears it, and maps
+// it to a status: a bounded wait that ran out is HTLR_ETIMEOUT, any other device check
+// HTLR_EDEVICE.  Clearing on read reports each failure once and leaves the handle usable.
+int check_device_error(const htlr_handle *H, const char *what)
+{
+    int err = 0;
+    HTLR_CK(cudaMemcpy(&err, H->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (!err) return HTLR_OK;
+    HTLR_CK(cudaMemsetAsync(H->d_err, 0, sizeof(int), H->stream));
+    HTLR_CK(cudaStreamSynchronize(H->stream));
+    char buf[160];
+    if (err == kDevTimeout) {
+        snprintf(buf, sizeof buf,
+                 "%s: a bounded device wait of a tensor-core kernel ran out (limit %lld SM "
+                 "cycles); the results of that matvec are invalid",
+                 what, (long long)H->tc_wait_cycles);
+        return fail(HTLR_ETIMEOUT, buf);
+    }
+    snprintf(buf, sizeof buf, "%s: device check failed (code %d)", what, err);
+    return fail(HTLR_EDEVICE, buf);
+}
+
 }  // namespace htlr
 
 using namespace htlr;
@@ -1541,6 +1565,7 @@ int htlr_construct_ex(htlr_handle **out, const htlr_kernel *k, int d, int n, con
     int q = (o && o->quad_order > 0) ? o->quad_order : 16;
     if (q > 64) return fail(HTLR_EINVAL, "quad_order must be in 1..64");
     if (o && o->tc_segment < 0) return fail(HTLR_EINVAL, "tc_segment must be >= 0");
+    if (o && o->tc_wait_cycles < 0) return fail(HTLR_EINVAL, "tc_wait_cycles must be >= 0");
     if (o && (o->orth < -1 || o->orth > 1)) return fail(HTLR_EINVAL, "orth must be -1, 0 or 1");
     if (o && (o->far_precision < 0 || o->far_precision > 3 || o->near_precision < 0 ||
               o->near_precision > 3))
@@ -1568,6 +1593,7 @@ int htlr_construct_ex(htlr_handle **out, const htlr_kernel *k, int d, int n, con
     H->far_prec = o ? o->far_precision : kPrecFP64;
     H->near_prec = o ? o->near_precision : kPrecFP64;
     if (o && o->tc_segment > 0) H->tc_seg_stages = o->tc_segment;
+    if (o && o->tc_wait_cycles > 0) H->tc_wait_cycles = o->tc_wait_cycles;
     int rc;
     try {
         rc = build(H, grid, o);
@@ -1621,7 +1647,7 @@ int htlr_matvec_timed(const htlr_handle *H, const double *u, double *f, int nrhs
     if (rc) return rc;
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     for (int k = 0; k < HTLR_NUM_STAGES; ++k) stage_ms[k] = tev.ms[k];
-    return HTLR_OK;
+    return check_device_error(H, "htlr_matvec_timed");
 }
 
 int htlr_matvec_host(htlr_handle *H, const double *u_host, double *f_host, int nrhs)
@@ -1647,7 +1673,7 @@ int htlr_matvec_host(htlr_handle *H, const double *u_host, double *f_host, int n
     HTLR_CK(cudaMemcpyAsync(f_host, H->d_stage_f, need * sizeof(double), cudaMemcpyDeviceToHost,
                             H->stream));
     HTLR_CK(cudaStreamSynchronize(H->stream));
-    return HTLR_OK;
+    return check_device_error(H, "htlr_matvec_host");
 }
 
 void htlr_free(htlr_handle *H)
@@ -1684,13 +1710,15 @@ int htlr_sync(const htlr_handle *H)
 {
     if (!is_live(H)) return fail(HTLR_EINVAL, "not a live HTLR handle");
     HTLR_CK(cudaStreamSynchronize(H->stream));
-    int err = 0;
-    HTLR_CK(cudaMemcpy(&err, H->d_err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (err) {
-        char buf[96];
-        snprintf(buf, sizeof buf, "device check failed (code %d)", err);
-        return fail(HTLR_EDEVICE, buf);
-    }
+    return check_device_error(H, "htlr_sync");
+}
+
+int htlr_set_wait_limit(htlr_handle *H, long long cycles)
+{
+    if (!is_live(H)) return fail(HTLR_EINVAL, "not a live HTLR handle");
+    if (cycles < 0) return fail(HTLR_EINVAL, "the wait limit must be >= 0");
+    H->tc_wait_cycles = cycles > 0 ? cycles : 4000000000ll;
+    ++H->generation;   // captured plans hold the old limit in their launch arguments
     return HTLR_OK;
 }
 

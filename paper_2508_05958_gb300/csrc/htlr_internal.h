@@ -199,6 +199,7 @@ struct htlr_handle {
     size_t task_bytes = 256 * 1024;
     int stream_ctas_per_sm = 8, stream_threads = 256, tc_stages_cap = 0;
     int tc_seg_stages = 8;   // grouped tensor-core kernel: K stages per FP32 accumulation
+    long long tc_wait_cycles = 4000000000ll;  // tensor-core kernels: bounded-wait limit
     int generation = 0;
     htlr_stats stats{};
     std::vector<void *> allocs;
@@ -209,6 +210,9 @@ namespace htlr {
 // Error reporting (thread-local message).
 void set_error(const std::string &msg);
 int cuda_fail(cudaError_t e, const char *what);
+// After the handle's stream has drained: read and clear its device error word
+// (HTLR_ETIMEOUT for a bounded wait that ran out, HTLR_EDEVICE for other checks).
+int check_device_error(const htlr_handle *H, const char *what);
 
 // ---- plan.cu: block cluster tree walk -------------------------------------------
 // Counts (pass 0) or fills (pass 1) the far and near lists of level `level` from the
@@ -351,6 +355,7 @@ struct TcgArgs {
     int *counter;                      // next group (reset to 0 before each launch)
     const int *order;                  // groups, heaviest first
     int seg_stages;                    // stages accumulated in TMEM before a drain to FP64
+    long long wait_cycles;             // limit of each bounded wait (SM clock cycles)
 };
 void launch_tcg_pack_blocks(const double *src, long long nblk, int ld, int Nd, int Kd, int nch,
                             int NGb, uint16_t *dst, cudaStream_t s);
@@ -373,6 +378,7 @@ struct TcArgs {
     int mtiles, kc, nchunks, Rp, nr, rows, ld, stages, tmem_cols;
     double *part;
     int *err;
+    long long wait_cycles;     // limit of each bounded wait (SM clock cycles)
 };
 void launch_tc_stream(const TcArgs &a, cudaStream_t s);
 // Shared-memory bytes of one pipeline stage (A chunk + B chunk, all splits).

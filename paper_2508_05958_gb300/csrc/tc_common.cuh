@@ -11,7 +11,15 @@ namespace htlr {
 namespace tcc {
 
 constexpr int kSplits = 3;
-constexpr long long kWaitCycles = 4000000000ll;  // about 2 s at 2 GHz
+// Default limit of a bounded device wait, in SM clock cycles: about 2 s at 2 GHz.  The
+// kernels take their limit from the launch arguments (htlr_options.tc_wait_cycles); the
+// waits of the clean-up after an abort, which must see copies and MMAs already in flight
+// land, always use this one.
+constexpr long long kWaitCycles = 4000000000ll;
+// Limits below this many cycles poll with the non-blocking mbarrier.test_wait, so that
+// they hold to within a few polls; longer ones let mbarrier.try_wait suspend the thread
+// between polls.
+constexpr long long kPollBelow = 1ll << 20;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -32,20 +40,40 @@ __device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count));
 }
 
-// Bounded wait for the phase with the given parity; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity)
+// One poll of the phase with the given parity: true once it has completed.  `suspend`
+// lets the hardware hold the thread for a while before answering (try_wait); otherwise
+// the answer is immediate (test_wait).
+__device__ __forceinline__ bool mbar_poll(uint64_t *b, uint32_t parity, bool suspend)
 {
-    const long long t0 = clock64();
-    while (true) {
-        uint32_t done;
+    uint32_t done;
+    if (suspend)
         asm volatile(
             "{\n .reg .pred P1;\n mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n"
             " selp.b32 %0, 1, 0, P1;\n}"
             : "=r"(done)
             : "r"(smem_u32(b)), "r"(parity)
             : "memory");
-        if (done) return true;
-        if (clock64() - t0 > kWaitCycles) return false;
+    else
+        asm volatile(
+            "{\n .reg .pred P1;\n mbarrier.test_wait.parity.shared::cta.b64 P1, [%1], %2;\n"
+            " selp.b32 %0, 1, 0, P1;\n}"
+            : "=r"(done)
+            : "r"(smem_u32(b)), "r"(parity)
+            : "memory");
+    return done != 0;
+}
+
+// Bounded wait for the phase with the given parity; false after `limit` SM cycles, or at
+// once when *abort_flag (may be null) is set by another role of the CTA.
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity,
+                                          long long limit = kWaitCycles,
+                                          volatile int *abort_flag = nullptr)
+{
+    const bool suspend = limit >= kPollBelow;
+    const long long t0 = clock64();
+    while (true) {
+        if (mbar_poll(b, parity, suspend)) return true;
+        if ((abort_flag && *abort_flag) || clock64() - t0 > limit) return false;
     }
 }
 

@@ -40,8 +40,9 @@
 // next.  At the end of a pass the sums are written as the FP64 partials of the group's
 // rows.
 // Groups are taken heaviest first from an atomic counter over a host-sorted order, so
-// the SMs finish together.  Every wait is bounded: on timeout the kernel records
-// kDevTimeout, drains what it issued and frees TMEM.
+// the SMs finish together.  Every wait is bounded (A.wait_cycles SM cycles): on timeout
+// the kernel records kDevTimeout, waits (with the long default limit) for the copies and
+// MMAs it has issued, frees TMEM and returns.
 #include <cuda.h>
 
 #include "tc_common.cuh"
@@ -150,23 +151,6 @@ void launch_tcg_pack_x(const double *W, long long w_box_stride, int Kd, int nbox
 // ---------------------------------------------------------------------------------
 // The grouped stream.
 // ---------------------------------------------------------------------------------
-// Bounded wait that also gives up when another role of the CTA has aborted.
-__device__ __forceinline__ bool wait_or_abort(uint64_t *b, uint32_t parity, volatile int *abort_flag)
-{
-    const long long t0 = clock64();
-    while (true) {
-        uint32_t done;
-        asm volatile(
-            "{\n .reg .pred P1;\n mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n"
-            " selp.b32 %0, 1, 0, P1;\n}"
-            : "=r"(done)
-            : "r"(smem_u32(b)), "r"(parity)
-            : "memory");
-        if (done) return true;
-        if (*abort_flag || clock64() - t0 > kWaitCycles) return false;
-    }
-}
-
 __global__ void __launch_bounds__(kGThreads, 1)
     tc_group_kernel(const __grid_constant__ CUtensorMap tmap, TcgArgs A)
 {
@@ -276,7 +260,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
                 for (long long q = 0; q < total; ++q, ++it_p) {
                     const int s = (int)(it_p % S);
                     if (it_p >= (uint32_t)S &&
-                        !wait_or_abort(&empty_bar[s], ((it_p / S) - 1) & 1, &abort_flag)) {
+                        !mbar_wait(&empty_bar[s], ((it_p / S) - 1) & 1, A.wait_cycles, &abort_flag)) {
                         abort_flag = 1;
                         break;
                     }
@@ -315,14 +299,14 @@ __global__ void __launch_bounds__(kGThreads, 1)
                     if (qs == 0) {
                         // the buffer's previous segment must be drained before it is reset
                         if (sc_m >= 2 &&
-                            !wait_or_abort(&seg_empty[buf], ((sc_m >> 1) - 1) & 1, &abort_flag)) {
+                            !mbar_wait(&seg_empty[buf], ((sc_m >> 1) - 1) & 1, A.wait_cycles, &abort_flag)) {
                             abort_flag = 1;
                             break;
                         }
                         asm volatile("tcgen05.fence::after_thread_sync;");
                     }
                     const int s = (int)(it_c % S);
-                    if (!wait_or_abort(&full_bar[s], (it_c / S) & 1, &abort_flag)) {
+                    if (!mbar_wait(&full_bar[s], (it_c / S) & 1, A.wait_cycles, &abort_flag)) {
                         abort_flag = 1;
                         break;
                     }
@@ -359,7 +343,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
                 for (int i = 0; i < kMaxDrainChunks * 8; ++i) acc[i] = 0.f;
                 for (long long sg = 0; sg < nseg; ++sg, ++sc_d) {
                     const uint32_t buf = sc_d & 1;
-                    if (!wait_or_abort(&seg_full[buf], (sc_d >> 1) & 1, &abort_flag)) {
+                    if (!mbar_wait(&seg_full[buf], (sc_d >> 1) & 1, A.wait_cycles, &abort_flag)) {
                         abort_flag = 1;
                         break;
                     }

@@ -19,8 +19,8 @@
 // the MMAs and commits them to the stage's "empty" mbarrier; S stages keep copies ahead
 // of the tensor core.  After the row, the four warps read the accumulator with
 // tcgen05.ld and write an FP64 partial for the usual fixed-order reduction.  Every wait
-// is bounded: on timeout the kernel records kDevTimeout, drains what it issued and frees
-// TMEM.
+// is bounded (A.wait_cycles SM cycles): on timeout the kernel records kDevTimeout, waits
+// (with the long default limit) for the copies and MMAs it issued, frees TMEM and returns.
 #include "tc_common.cuh"
 
 namespace htlr {
@@ -136,7 +136,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_stream_kernel(TcArgs A)
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ uint64_t full_bar[kTcMaxStages], empty_bar[kTcMaxStages], done_bar;
     __shared__ uint32_t tmem_holder;
-    __shared__ int abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int S = A.stages, mtiles = A.mtiles, kc = A.kc, Rp = A.Rp;
     const uint32_t sub_a = (uint32_t)(kTcM * kc * 2);   // bytes of one A sub-tile
@@ -150,7 +149,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_stream_kernel(TcArgs A)
             mbar_init(&empty_bar[s], 1);
         }
         mbar_init(&done_bar, 1);
-        abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -170,10 +168,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_stream_kernel(TcArgs A)
     const uint32_t b_lbo = (uint32_t)(Rp / 8) * 128, b_sbo = 128;
     // the six products a_i b_j with i + j <= 2 (0-based)
     const int pa[6] = {0, 0, 1, 0, 1, 2}, pb[6] = {0, 1, 0, 2, 1, 0};
-    // per-stage phase bookkeeping (thread 0 only)
-    uint32_t full_ph = 0, empty_ph = 0, pending = 0;  // bit s: parity / pending commit
+    // per-stage phase bookkeeping (thread 0 only); bit s of `loaded`: a copy into stage s
+    // whose completion has not been observed; of `pending`: MMAs committed to empty_bar[s]
+    // whose completion has not been observed
+    uint32_t full_ph = 0, empty_ph = 0, pending = 0, loaded = 0;
     uint32_t done_ph = 0;
+    int done_out = 0;           // thread 0: commits to done_bar not yet observed
+    __shared__ int row_ok;
     bool ok = true;
+    const long long lim = A.wait_cycles;
 
     for (int t = A.t0 + blockIdx.x; t < A.t1 && ok; t += gridDim.x) {
         const Task T = A.tasks[t];
@@ -183,7 +186,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_stream_kernel(TcArgs A)
             auto load = [&](long long q) -> bool {
                 const int s = (int)(q % S);
                 if (pending & (1u << s)) {  // the MMAs that read this stage must be done
-                    if (!mbar_wait(&empty_bar[s], (empty_ph >> s) & 1)) return false;
+                    if (!mbar_wait(&empty_bar[s], (empty_ph >> s) & 1, lim)) return false;
                     empty_ph ^= 1u << s;
                     pending &= ~(1u << s);
                 }
@@ -199,17 +202,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_stream_kernel(TcArgs A)
                              : "memory");
                 bulk_load(st, ga, a_chunk_bytes, &full_bar[s]);
                 bulk_load(st + a_chunk_bytes, gb, b_chunk_bytes, &full_bar[s]);
+                loaded |= 1u << s;
                 return true;
             };
             for (long long q = 0; q < total && q < S && ok; ++q) ok = load(q);
             asm volatile("tcgen05.fence::after_thread_sync;");
             for (long long q = 0; q < total && ok; ++q) {
                 const int s = (int)(q % S);
-                if (!mbar_wait(&full_bar[s], (full_ph >> s) & 1)) {
+                if (!mbar_wait(&full_bar[s], (full_ph >> s) & 1, lim)) {
                     ok = false;
                     break;
                 }
                 full_ph ^= 1u << s;
+                loaded &= ~(1u << s);
                 const uint32_t a_base = smem_u32(sm + (size_t)s * stage_bytes);
                 const uint32_t b_base = a_base + a_chunk_bytes;
                 for (int mt = 0; mt < mtiles; ++mt) {
@@ -231,26 +236,30 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_stream_kernel(TcArgs A)
                 // the tensor core always has the current chunk to work on meanwhile)
                 if (q >= 1 && q - 1 + S < total) ok = load(q - 1 + S);
             }
-            mma_commit(&done_bar);  // completes when every MMA issued so far is done
+            if (ok) {
+                // the row's MMAs: one commit, observed by thread 0 alone
+                mma_commit(&done_bar);
+                done_out = 1;
+                if (mbar_wait(&done_bar, done_ph, lim)) {
+                    done_ph ^= 1;
+                    done_out = 0;
+                } else {
+                    ok = false;
+                }
+            }
+            row_ok = ok ? 1 : 0;
         }
+        if (tid == 0 && total == 0) row_ok = 1;
         __syncthreads();
-        if (tid == 0 && !ok) abort_flag = 1;
-        __syncthreads();
-        if (abort_flag) {
+        const int rok = row_ok;
+        __syncthreads();   // every thread has read row_ok before thread 0 writes it again
+        if (!rok) {
             ok = false;
             break;
         }
         if (total == 0) continue;
-        // every thread waits for the row's MMAs; the outcome is agreed on block-wide so
-        // that all threads leave the loop together
-        const int late = __syncthreads_or(mbar_wait(&done_bar, done_ph) ? 0 : 1);
-        if (late) {
-            if (tid == 0) atomicExch(A.err, (int)kDevTimeout);
-            ok = false;
-        }
-        done_ph ^= 1;
         asm volatile("tcgen05.fence::after_thread_sync;");
-        if (ok) {
+        {
             // accumulator rows: warp w holds lanes 32 w .. 32 w + 31 of every M-tile
             double *out = A.part + T.part;
             for (int mt = 0; mt < mtiles; ++mt) {
@@ -278,11 +287,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_stream_kernel(TcArgs A)
     if (!ok) {
         if (tid == 0) {
             atomicExch(A.err, (int)kDevTimeout);
-            // drain: let every MMA issued by this CTA finish before TMEM is released
-            mma_commit(&done_bar);
+            // clean-up with the long default limit: every MMA this CTA issued finishes
+            // (one commit covers them all) and every copy it issued lands before TMEM and
+            // shared memory are released
+            if (!done_out) {
+                mma_commit(&done_bar);
+                done_out = 1;
+            }
             mbar_wait(&done_bar, done_ph);
             for (int s = 0; s < S; ++s)
                 if (pending & (1u << s)) mbar_wait(&empty_bar[s], (empty_ph >> s) & 1);
+            for (int s = 0; s < S; ++s)
+                if (loaded & (1u << s)) mbar_wait(&full_bar[s], (full_ph >> s) & 1);
         }
         __syncthreads();
     }

@@ -29,7 +29,7 @@ SYMBOLS = ("htlr_construct", "htlr_construct_ex", "htlr_matvec", "htlr_matvec_ti
            "htlr_plan_launches", "htlr_plan_free", "htlr_autotune", "htlr_autotune_clear_cache",
            "htlr_server_create", "htlr_server_add_operator", "htlr_server_submit",
            "htlr_server_poll", "htlr_server_wait", "htlr_server_get_stats",
-           "htlr_server_destroy", "htlr_tensor_flops")
+           "htlr_server_destroy", "htlr_tensor_flops", "htlr_set_wait_limit")
 
 
 class HTLRError(RuntimeError):
@@ -51,7 +51,7 @@ class htlr_options(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int), ("orth", ctypes.c_int), ("quad_order", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("hbm_limit", ctypes.c_size_t),
                 ("far_precision", ctypes.c_int), ("near_precision", ctypes.c_int),
-                ("tc_segment", ctypes.c_int)]
+                ("tc_segment", ctypes.c_int), ("tc_wait_cycles", ctypes.c_longlong)]
 
 
 class htlr_stats(ctypes.Structure):
@@ -172,6 +172,8 @@ def load(build_if_missing: bool = True):
         L.htlr_set_stream.restype = ctypes.c_int
         L.htlr_sync.argtypes = [vp]
         L.htlr_sync.restype = ctypes.c_int
+        L.htlr_set_wait_limit.argtypes = [vp, ctypes.c_longlong]
+        L.htlr_set_wait_limit.restype = ctypes.c_int
         L.htlr_last_error.argtypes = []
         L.htlr_last_error.restype = ctypes.c_char_p
         L.htlr_last_launch_count.argtypes = [vp]
@@ -233,7 +235,7 @@ def _hptr(a):
 
 def htlr_construct(ktype, d, n, leaf, r, eta, *, kscale=1.0, kparam=0.0, a=None, grid=None,
                    storage=STORE_AUTO, orth=-1, quad_order=0, stream=None, hbm_limit=0,
-                   far_precision=0, near_precision=0, tc_segment=0):
+                   far_precision=0, near_precision=0, tc_segment=0, tc_wait_cycles=0):
     """Construct (Algorithm 1).  ``a``: host array of N values (natural order) or None.
     ``grid``: None (uniform) or (coords (d, n), edges (d, n+1)).  Returns an opaque handle
     (int).  ``stream``: a torch.cuda.Stream, a raw cudaStream_t int, or None."""
@@ -254,7 +256,7 @@ def htlr_construct(ktype, d, n, leaf, r, eta, *, kscale=1.0, kparam=0.0, a=None,
         keep.append(a)
         g.a = _hptr(a)
     o = htlr_options(storage, orth, quad_order, _stream_ptr(stream), hbm_limit, far_precision,
-                     near_precision, tc_segment)
+                     near_precision, tc_segment, tc_wait_cycles)
     h = ctypes.c_void_p()
     _check(L.htlr_construct_ex(ctypes.byref(h), ctypes.byref(k), d, n, ctypes.byref(g), leaf, r,
                                eta, ctypes.byref(o)))
@@ -333,7 +335,14 @@ def htlr_set_stream(H, stream):
 
 
 def htlr_sync(H):
+    """Wait for the handle's stream; raise HTLRError (code HTLR_ETIMEOUT or HTLR_EDEVICE)
+    if a device check failed since the last report (the report clears it)."""
     _check(load().htlr_sync(H))
+
+
+def htlr_set_wait_limit(H, cycles):
+    """Bounded-wait limit of the tensor-core kernels in SM cycles (0: the default)."""
+    _check(load().htlr_set_wait_limit(H, int(cycles)))
 
 
 def htlr_last_launch_count(H) -> int:

@@ -112,6 +112,10 @@ def replay(server, ops, stream, op_ids=None, keep_solutions=False):
     wall = time.perf_counter() - t0
     infos = [inf for _, inf in results]
     lat = [inf["done_s"] - inf["submit_s"] for inf in infos]
+    # service time: admission (a slot and memory granted) to completion; queueing: the
+    # wait from submission to admission
+    svc = [inf["done_s"] - inf["admit_s"] for inf in infos]
+    queue = [inf["admit_s"] - inf["submit_s"] for inf in infos]
     first = min(inf["submit_s"] for inf in infos)
     last = max(inf["done_s"] for inf in infos)
     out = {
@@ -121,6 +125,10 @@ def replay(server, ops, stream, op_ids=None, keep_solutions=False):
         "p50_ms": 1e3 * percentile(lat, 50),
         "p99_ms": 1e3 * percentile(lat, 99),
         "mean_ms": 1e3 * float(np.mean(lat)),
+        "service_p50_ms": 1e3 * percentile(svc, 50),
+        "service_p99_ms": 1e3 * percentile(svc, 99),
+        "queue_p50_ms": 1e3 * percentile(queue, 50),
+        "queue_p99_ms": 1e3 * percentile(queue, 99),
         "solves_per_s": len(ids) / (last - first),
         "makespan_s": last - first,
         "wall_s": wall,

@@ -503,3 +503,38 @@ def test_block_ranges_partition_the_product(oracle):
         assert work == expect
     finally:
         H.free()
+
+
+@pytest.mark.parametrize("case", [dict(d=3, n=16, leaf=4, p=5, eta=1.0, k=1),
+                                  dict(d=2, n=64, leaf=8, p=6, eta=math.sqrt(2.0), k=0),
+                                  dict(d=3, n=16, leaf=2, p=3, eta=0.0, k=2, tensor=True)])
+def test_parallel_matvec_is_the_serial_block_loop_bitwise(oracle, case):
+    """HMultVec runs the per-block products of Algorithm 2 on all host cores and adds them
+    leaf box by leaf box in recursion order.  Every element of f must receive the same
+    additions in the same order as in the serial block loop (matvec_range over all blocks
+    into a zero f), so the results agree bit for bit, for any thread count and for
+    several right-hand sides, on uniform and tensor grids."""
+    from paper_2508_05958_gb300.workloads import quasi_uniform_tensor_grid
+    d, n = case["d"], case["n"]
+    grid = quasi_uniform_tensor_grid(d, n, seed=8) if case.get("tensor") else None
+    kw = dict(grid=grid, orth=False) if grid is not None else {}
+    H = oracle.HTLR(d, n, case["k"], case["leaf"], case["p"], case["eta"],
+                    a=np.linspace(0.5, 1.5, n ** d), **kw)
+    before = oracle.num_threads()
+    try:
+        rng = np.random.default_rng(21)
+        U = np.asfortranarray(rng.standard_normal((n ** d, 3)))
+        serial = np.zeros_like(U, order="F")
+        for c in range(3):
+            col = np.zeros(n ** d)
+            H.matvec_range(np.ascontiguousarray(U[:, c]), col, 0, H.nblocks())
+            serial[:, c] = col
+        outs = []
+        for threads in (1, 3, max(4, before)):
+            oracle.set_num_threads(threads)
+            outs.append(H.matvec(U))
+        for f in outs:
+            assert np.array_equal(f, serial)
+    finally:
+        oracle.set_num_threads(before)
+        H.free()
