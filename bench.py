@@ -43,6 +43,10 @@ def parse():
     ap.add_argument("--far-precision", type=int, default=1, help="0 FP64, 1 DF64, 2 FP32, 3 BF16X6 (tensor cores)")
     ap.add_argument("--near-precision", type=int, default=1, help="0 FP64, 1 DF64, 2 FP32, 3 BF16X6 (tensor cores)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tc-segment", type=int, default=0,
+                    help="tensor-core K steps per accumulator segment (0: library default)")
+    ap.add_argument("--tc-flush", type=int, default=0,
+                    help="tensor-core segments per FP64 flush (0: library default)")
     ap.add_argument("--gmres-solves", type=int, default=20,
                     help="GMRES solves (to 1e-10) timed after the matvec, per variant")
     ap.add_argument("--cpu-sample-s", type=float, default=20.0)
@@ -631,7 +635,7 @@ def run_gpu(args, w):
     t0 = time.perf_counter()
     H = htlr.htlr_construct(w.ktype, w.d, w.n, w.leaf, w.p, w.eta, kscale=w.kscale,
                             kparam=w.kparam, a=w.a(), grid=w.grid(), storage=args.storage,
-                            stream=stream,
+                            stream=stream, tc_segment=args.tc_segment, tc_flush=args.tc_flush,
                             far_precision=args.far_precision, near_precision=args.near_precision)
     torch.cuda.synchronize()
     construct_s = time.perf_counter() - t0

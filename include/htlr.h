@@ -103,16 +103,14 @@ typedef enum {
     HTLR_PREC_BF16X6 = 3 /* tensor cores (tcgen05): operands split into three BF16 terms,
                             the six products a_i b_j with i + j <= 4 (1-based) accumulated
                             in FP32 tensor memory; the many-right-hand-side path, 64 RHS at
-                            a time.  The tensor cores' FP32 accumulation loses ~2e-8
-                            relative per accumulated MMA, so the error grows with the
-                            accumulation length.  With SHARED blocks the accumulation runs
-                            in segments of tc_segment K steps whose sums are added in FP32
-                            registers (measured 1.8e-6 relative on the n = 128 operator);
-                            with STORED blocks a whole block row accumulates in tensor
-                            memory (~1e-6 on small operators, up to ~1e-3 on long rows).
-                            A BF16X6 far field goes
-                            with a BF16X6, generated, or held FP64/df64/FP32 near field;
-                            a BF16X6 near field needs a BF16X6 far field */
+                            a time.  The tensor cores' FP32 accumulation truncates each
+                            addition, so with SHARED blocks the accumulation runs in short
+                            segments (tc_segment) that start fresh with the small cross
+                            products, whose sums are added in FP32 registers and flushed to
+                            FP64 every tc_flush segments.  With STORED blocks a whole block
+                            row accumulates in tensor memory (see htlr_options).  A BF16X6
+                            far field goes with a BF16X6, generated, or held FP64/df64/FP32
+                            near field; a BF16X6 near field needs a BF16X6 far field */
 } htlr_precision;
 
 typedef struct {
@@ -126,11 +124,15 @@ typedef struct {
     size_t hbm_limit;  /* maximum bytes the handle may allocate (0: 90% of free memory) */
     int far_precision;   /* htlr_precision of the admissible blocks (default FP64) */
     int near_precision;  /* htlr_precision of the inadmissible blocks (default FP64) */
-    int tc_segment;      /* BF16X6 with SHARED blocks: K steps of 16 columns accumulated in
-                            FP32 tensor memory before they are added to the FP64 result
-                            (0: default 8).  The FP32 accumulation of the tensor cores loses
-                            about 2^-25 relative per MMA, so shorter segments are more
-                            accurate and drain more often */
+    int tc_segment;      /* BF16X6 with SHARED blocks: K steps of 16 columns per tensor-memory
+                            segment (0: default 4).  A
+                            segment starts from a fresh accumulator; its cross products
+                            (a3b1, a2b2, a1b3, a2b1, a1b2) are accumulated first, while the
+                            sum is small, and the leading products a1b1 last, because the
+                            tensor cores' FP32 accumulation truncates every addition (about
+                            2^-24 of the running sum, biased toward zero) */
+    int tc_flush;        /* BF16X6 with SHARED blocks: segments summed in FP32 registers before
+                            they are added to the FP64 result (0: default 32) */
     long long tc_wait_cycles; /* limit, in SM clock cycles, of every bounded wait inside the
                             tensor-core kernels (a copy, an MMA or a drain that does not
                             complete): 0 selects the default 4e9 (about 2 s at 2 GHz).  When

@@ -144,33 +144,6 @@ struct Sizes {
     size_t total() const { return cores + near + factors + work + lists; }
 };
 
-// Packed split-BF16 shape of rows x cols blocks: 128-row M-tiles; the K chunk is the
-// largest of 64, 32, 16 columns for which three pipeline stages of (A chunk + B chunk for
-// kTcRpMax right-hand sides) fit in 210 KB of shared memory.
-static TcShape tc_shape(int rows, int cols)
-{
-    TcShape t;
-    t.rows = rows;
-    t.cols = cols;
-    t.mtiles = (rows + 127) / 128;
-    for (int kc : {64, 32, 16}) {  // BF16 MMAs take K in steps of 16
-        t.kc = kc;
-        if (tc_stage_bytes(t.mtiles, kc, kTcRpMax) * 3 <= 210 * 1024) break;
-    }
-    t.nchunks = (cols + t.kc - 1) / t.kc;
-    t.blk_elems = (long long)t.nchunks * 3 * t.mtiles * 128 * t.kc;
-    t.x_elems = (long long)t.nchunks * 3 * kTcRpMax * t.kc;
-    return t;
-}
-
-// Pipeline depth for a shape and a right-hand-side count (at most 210 KB of stages).
-static int tc_stages(const TcShape &t, int Rp)
-{
-    int S = (int)((210 * 1024) / tc_stage_bytes(t.mtiles, t.kc, Rp));
-    if (S > kTcMaxStages) S = kTcMaxStages;
-    return S < 2 ? 2 : S;
-}
-
 // Grouped tensor-core shape of Nd x Kd blocks (see tc_group.cu).
 static TcgShape tcg_shape(int Nd, int Kd)
 {
@@ -178,10 +151,12 @@ static TcgShape tcg_shape(int Nd, int Kd)
     t.Kd = Kd;
     t.Nd = Nd;
     t.nch = (Kd + 15) / 16;
-    t.Npad = (Nd + 15) / 16 * 16;
-    if (t.Npad > 256) t.Npad = (Nd + 31) / 32 * 32;   // two passes of Npad / 2 (a multiple of 16)
-    t.passes = t.Npad > 256 ? 2 : 1;
-    t.Nw = t.Npad / t.passes;
+    // passes of at most kTcgMaxNw rows: two accumulator buffers of Nw columns fit in tensor
+    // memory, and a drain thread holds Nw / 2 running sums in registers
+    const int n16 = (Nd + 15) / 16 * 16;
+    t.passes = (n16 + kTcgMaxNw - 1) / kTcgMaxNw;
+    t.Nw = ((Nd + t.passes - 1) / t.passes + 15) / 16 * 16;
+    t.Npad = t.Nw * t.passes;
     t.NGb = t.Npad / 8;
     t.core_elems = (long long)t.nch * 3 * t.NGb * 128;
     t.box_elems = (long long)3 * t.nch * (kTcRpMax / 8) * 128;
@@ -519,9 +494,9 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
         Lv.ld = round_up(Lv.pd, 32);
         if (Lv.ld / 32 > 16)
             return fail(HTLR_EUNSUPPORTED, "p_eff^d above 512 is not supported");
-        Lv.tc = tc_shape(Lv.pd, Lv.pd);
+        Lv.tg = tcg_shape(Lv.pd, Lv.pd);
     }
-    H->near_tc = tc_shape(rows_leaf, rows_leaf);
+    H->near_tg = tcg_shape(rows_leaf, rows_leaf);
     // tensor-core stream: the far field on the tensor cores, the near field on the tensor
     // cores too, generated, or held in FP64 / df64 / FP32 for the CUDA-core stream
     if (H->near_prec == kPrecBF16X6 && (H->far_prec != kPrecBF16X6 || H->near_generated))
@@ -596,7 +571,7 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
     for (int lv = 1; lv <= L; ++lv) {
         LevelData &Lv = H->lev[lv];
         if (Lv.nfar == 0) continue;
-        size_t blk = H->tc ? (size_t)Lv.tc.blk_elems * 4
+        size_t blk = H->tc ? (size_t)Lv.tg.core_elems * 2
                            : (size_t)Lv.ld * Lv.pd * prec_bytes(H->far_prec);
         // tensor-core tasks are whole block rows (one per row)
         auto ct = count_tasks(Lv.far_rowptr, Lv.nbox, H->tc ? 1 : blk);
@@ -625,7 +600,7 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
         }
     } else {
         size_t blk = H->near_prec == kPrecBF16X6
-                         ? (size_t)H->near_tc.blk_elems * 4
+                         ? (size_t)H->near_tg.core_elems * 2
                          : (size_t)H->near_ld * rows_leaf * prec_bytes(H->near_prec);
         auto ct = count_tasks(H->near_rowptr, 1 << (d * L), H->near_prec == kPrecBF16X6 ? 1 : blk);
         ntasks += ct.first;
@@ -653,6 +628,15 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
     }
     if (want != HTLR_STORE_STORED && want != HTLR_STORE_SHARED)
         return fail(HTLR_EINVAL, "options.storage must be AUTO, STORED, SHARED or GENERATED");
+    if (H->tc && want == HTLR_STORE_STORED) {
+        if (o && o->storage == HTLR_STORE_STORED)
+            return fail(HTLR_EUNSUPPORTED,
+                        "BF16X6 block lists are held one block per level and box offset "
+                        "(SHARED or GENERATED storage), where the grouped tensor-core kernel "
+                        "reads each block once for a group of targets; STORED blocks take "
+                        "FP64, df64 or FP32");
+        want = HTLR_STORE_SHARED;
+    }
     const Sizes &sz = (want == HTLR_STORE_STORED) ? sz_stored : sz_shared;
     if (sz.total() > limit) {
         char buf[256];
@@ -771,28 +755,29 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
                 Lv.d_cores = f32;
             }
             if (H->far_prec == kPrecBF16X6) {
-                // packed split-BF16 chunks for the tensor-core stream: grouped by target
-                // (one block per offset, SHARED) when the level's offsets form classes
+                // packed split-BF16 chunks for the grouped tensor-core stream (one block per
+                // offset): the level's offsets must form parity classes
                 std::vector<int4v> cl;
                 Lv.tg = tcg_shape(Lv.pd, Lv.pd);
-                Lv.tcg = !stored && Lv.tg.Npad <= 512 &&
-                         build_classes(d, 1 << lv, Lv.far_rowptr, Lv.far_col, Lv.far_core, cl,
+                Lv.tcg = build_classes(d, 1 << lv, Lv.far_rowptr, Lv.far_col, Lv.far_core, cl,
                                        Lv.cls_start, Lv.cls_count);
-                if (Lv.tcg) {
-                    Lv.h_cls = cl;
-                    if (dalloc(H, &Lv.d_cls, cl.size())) return HTLR_ECUDA;
-                    HTLR_CK(cudaMemcpyAsync(Lv.d_cls, cl.data(), sizeof(int4v) * cl.size(),
-                                            cudaMemcpyHostToDevice, s));
+                if (!Lv.tcg) {
+                    cudaFree(dcore);
+                    return fail(HTLR_EUNSUPPORTED, "BF16X6: the admissible offsets of a level do "
+                                                   "not form parity classes");
                 }
+                Lv.h_cls = cl;
+                if (dalloc(H, &Lv.d_cls, cl.size())) {
+                    cudaFree(dcore);
+                    return HTLR_ECUDA;
+                }
+                HTLR_CK(cudaMemcpyAsync(Lv.d_cls, cl.data(), sizeof(int4v) * cl.size(),
+                                        cudaMemcpyHostToDevice, s));
                 uint16_t *pk = nullptr;
-                int rc2 = dalloc(H, &pk, (size_t)Lv.ncores * (Lv.tcg ? Lv.tg.core_elems
-                                                                     : Lv.tc.blk_elems));
-                if (rc2 == HTLR_OK && Lv.tcg)
+                int rc2 = dalloc(H, &pk, (size_t)Lv.ncores * Lv.tg.core_elems);
+                if (rc2 == HTLR_OK)
                     launch_tcg_pack_blocks(dcore, Lv.ncores, Lv.ld, Lv.pd, Lv.pd, Lv.tg.nch,
                                            Lv.tg.NGb, pk, s);
-                else if (rc2 == HTLR_OK)
-                    launch_tc_pack_blocks(dcore, Lv.ncores, Lv.ld, Lv.pd, Lv.pd, Lv.tc.mtiles,
-                                          Lv.tc.kc, Lv.tc.nchunks, pk, s);
                 cudaError_t e2 = cudaStreamSynchronize(s);
                 cudaFree(dcore);
                 if (rc2) return rc2;
@@ -922,24 +907,25 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
             HTLR_CK(cudaStreamSynchronize(s));
             std::vector<int4v> cl;
             H->near_tg = tcg_shape(rows_leaf, rows_leaf);
-            H->near_tcg = !stored && H->near_tg.Npad <= 512 &&
-                          build_classes(d, 1 << L, H->near_rowptr, H->near_col, H->near_blk, cl,
+            H->near_tcg = build_classes(d, 1 << L, H->near_rowptr, H->near_col, H->near_blk, cl,
                                         H->near_cls_start, H->near_cls_count);
-            if (H->near_tcg) {
-                H->h_near_cls = cl;
-                if (dalloc(H, &H->d_near_cls, cl.size())) return HTLR_ECUDA;
-                HTLR_CK(cudaMemcpyAsync(H->d_near_cls, cl.data(), sizeof(int4v) * cl.size(),
-                                        cudaMemcpyHostToDevice, s));
+            if (!H->near_tcg) {
+                cudaFree(dnear);
+                return fail(HTLR_EUNSUPPORTED, "BF16X6: the inadmissible offsets of the leaves "
+                                               "do not form parity classes");
             }
+            H->h_near_cls = cl;
+            if (dalloc(H, &H->d_near_cls, cl.size())) {
+                cudaFree(dnear);
+                return HTLR_ECUDA;
+            }
+            HTLR_CK(cudaMemcpyAsync(H->d_near_cls, cl.data(), sizeof(int4v) * cl.size(),
+                                    cudaMemcpyHostToDevice, s));
             uint16_t *pk = nullptr;
-            int rc2 = dalloc(H, &pk, (size_t)H->nnear_unique * (H->near_tcg ? H->near_tg.core_elems
-                                                                            : H->near_tc.blk_elems));
-            if (rc2 == HTLR_OK && H->near_tcg)
+            int rc2 = dalloc(H, &pk, (size_t)H->nnear_unique * H->near_tg.core_elems);
+            if (rc2 == HTLR_OK)
                 launch_tcg_pack_blocks(dnear, H->nnear_unique, H->near_ld, rows_leaf, rows_leaf,
                                        H->near_tg.nch, H->near_tg.NGb, pk, s);
-            else if (rc2 == HTLR_OK)
-                launch_tc_pack_blocks(dnear, H->nnear_unique, H->near_ld, rows_leaf, rows_leaf,
-                                      H->near_tc.mtiles, H->near_tc.kc, H->near_tc.nchunks, pk, s);
             cudaError_t e2 = cudaStreamSynchronize(s);
             cudaFree(dnear);
             if (rc2) return rc2;
@@ -1015,12 +1001,10 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
         for (int lv = 1; lv <= L; ++lv) {
             LevelData &Lv = H->lev[lv];
             if (Lv.nfar == 0) continue;
-            Lv.tc_t0 = (int)H->tasks_tc.size();
             row_tasks(lv, Lv.far_rowptr, Lv.nbox, Lv.ld, Lv.row_task_tc);
-            Lv.tc_t1 = (int)H->tasks_tc.size();
             if (dalloc(H, &Lv.d_row_task_tc, Lv.row_task_tc.size()))
                 return HTLR_ECUDA;
-            if (Lv.tcg) {
+            {
                 if (dalloc(H, &Lv.d_Wg, (size_t)Lv.nbox * Lv.tg.box_elems)) return HTLR_ECUDA;
                 for (int k = 0; k < 3; ++k) {
                     if (tcg_encode_source_map(Lv.tmap[k].b, Lv.d_Wg, Lv.tg.nch, 16 << k, 1 << lv, d))
@@ -1032,18 +1016,14 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
                                             cudaMemcpyHostToDevice, s));
                     HTLR_CK(cudaStreamSynchronize(s));
                 }
-            } else if (dalloc(H, &Lv.d_Wp, (size_t)Lv.nbox * Lv.tc.x_elems)) {
-                return HTLR_ECUDA;
             }
             HTLR_CK(cudaMemcpyAsync(Lv.d_row_task_tc, Lv.row_task_tc.data(),
                                     sizeof(int) * Lv.row_task_tc.size(), cudaMemcpyHostToDevice, s));
         }
         if (H->near_prec == kPrecBF16X6) {
-            H->near_tc_t0 = (int)H->tasks_tc.size();
             row_tasks(L + 1, H->near_rowptr, 1 << (d * L), H->near_ld, H->near_row_task_tc);
-            H->near_tc_t1 = (int)H->tasks_tc.size();
             if (dalloc(H, &H->d_near_row_task_tc, H->near_row_task_tc.size())) return HTLR_ECUDA;
-            if (H->near_tcg) {
+            {
                 if (dalloc(H, &H->d_Ug, (size_t)(1 << (d * L)) * H->near_tg.box_elems))
                     return HTLR_ECUDA;
                 for (int k = 0; k < 3; ++k) {
@@ -1057,8 +1037,6 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
                                             cudaMemcpyHostToDevice, s));
                     HTLR_CK(cudaStreamSynchronize(s));
                 }
-            } else if (dalloc(H, &H->d_Up, (size_t)(1 << (d * L)) * H->near_tc.x_elems)) {
-                return HTLR_ECUDA;
             }
             HTLR_CK(cudaMemcpyAsync(H->d_near_row_task_tc, H->near_row_task_tc.data(),
                                     sizeof(int) * H->near_row_task_tc.size(),
@@ -1268,37 +1246,8 @@ int run_chunk(const htlr_handle *H, const KindDesc *d_kinds, double *part,
     mark(1);
     mark(2);
     if (H->tc) {
-        // tensor-core stream: pack the source operands, then one launch per block list
-        const int Rp = ((nh + 15) / 16) * 16;
-        auto tc_launch = [&](const TcShape &ts, int t0, int t1, const int *col, const int *blk,
-                             const void *blocks, const uint16_t *x, int rows, int ld) {
-            TcArgs a{};
-            a.tasks = H->d_tasks_tc;
-            a.t0 = t0;
-            a.t1 = t1;
-            a.col = col;
-            a.blk = blk;
-            a.blocks = static_cast<const uint16_t *>(blocks);
-            a.blk_elems = ts.blk_elems;
-            a.x = x;
-            a.x_box_elems = (long long)ts.nchunks * 3 * Rp * ts.kc;
-            a.mtiles = ts.mtiles;
-            a.kc = ts.kc;
-            a.nchunks = ts.nchunks;
-            a.Rp = Rp;
-            a.nr = nh;
-            a.rows = rows;
-            a.ld = ld;
-            a.stages = tc_stages(ts, Rp);
-            if (H->tc_stages_cap >= 2 && a.stages > H->tc_stages_cap) a.stages = H->tc_stages_cap;
-            int cols = 32;
-            while (cols < ts.mtiles * Rp) cols *= 2;
-            a.tmem_cols = cols;
-            a.part = H->d_part_tc;
-            a.err = H->d_err;
-            a.wait_cycles = H->tc_wait_cycles;
-            launch_tc_stream(a, s);
-        };
+        // tensor-core stream: pack the source operands, then one grouped launch per
+        // block list
         // grouped path: G = 128 / Rpg targets per MMA
         const int Rpg = nh <= 16 ? 16 : nh <= 32 ? 32 : 64, tmi = Rpg == 16 ? 0 : Rpg == 32 ? 1 : 2;
         auto tcg_launch = [&](const TcgShape &tg, const int4v *cls, const int *cs, const int *cc,
@@ -1307,7 +1256,6 @@ int run_chunk(const htlr_handle *H, const KindDesc *d_kinds, double *part,
             TcgArgs g{};
             g.counter = counter;
             g.order = order;
-            g.seg_stages = H->tc_seg_stages;
             g.offs = reinterpret_cast<const int4 *>(cls);
             for (int c = 0; c < 8; ++c) {
                 g.cls_start[c] = cs[c];
@@ -1332,10 +1280,25 @@ int run_chunk(const htlr_handle *H, const KindDesc *d_kinds, double *part,
             g.row_task = row_task;
             g.part = H->d_part_tc;
             g.ld = ld;
-            int S = (int)((200 * 1024) / tcg_stage_bytes(tg.Nw / 8));
-            if (S > kTcMaxStages) S = kTcMaxStages;
-            if (H->tc_stages_cap >= 2 && S > H->tc_stages_cap) S = H->tc_stages_cap;
-            g.stages = S < 2 ? 2 : S;
+            // copy rings within 200 KB of shared memory: the lead ring holds a segment's
+            // stages until its leading products are issued (at least F slots, or the copies
+            // of the segment's last stages would wait for its own leading products; two
+            // segments where they fit); the cross ring takes the rest.  The segment length
+            // fixes the summation order, so it is never changed by the ring depths (tuned)
+            const size_t lb = tcg_lead_bytes(tg.Nw / 8), cb = tcg_cross_bytes(tg.Nw / 8);
+            const size_t budget = 200 * 1024;
+            int F = std::max(1, H->tc_seg_stages);
+            while (F > 1 && (size_t)F * lb + 2 * cb > budget) --F;   // only for huge F
+            if (F > kTcMaxLead) F = kTcMaxLead;
+            int Sl = std::min(kTcMaxLead, 2 * F);
+            while (Sl > F && (size_t)Sl * lb + 2 * cb > budget) --Sl;
+            int Sc = (int)((budget - (size_t)Sl * lb) / cb);
+            if (Sc > kTcMaxStages) Sc = kTcMaxStages;
+            if (H->tc_stages_cap >= 2 && Sc > H->tc_stages_cap) Sc = H->tc_stages_cap;
+            g.stages = Sc < 2 ? 2 : Sc;
+            g.lead_stages = Sl;
+            g.seg_stages = F;
+            g.flush_segs = H->tc_flush_segs;
             int cols = 32;
             while (cols < 2 * tg.Nw) cols *= 2;   // two accumulator buffers
             g.tmem_cols = cols;
@@ -1346,32 +1309,18 @@ int run_chunk(const htlr_handle *H, const KindDesc *d_kinds, double *part,
         for (int lv = 1; lv <= L; ++lv) {
             const LevelData &Lv = H->lev[lv];
             if (Lv.nfar == 0) continue;
-            if (Lv.tcg) {
-                launch_tcg_pack_x(W[lv], (long long)H->nrc * Lv.pd, Lv.pd, Lv.nbox, nh, Rpg,
-                                  Lv.tg.nch, 0, d, n, H->leaf, L, nullptr, 0, Lv.d_Wg, s);
-                tcg_launch(Lv.tg, Lv.d_cls, Lv.cls_start, Lv.cls_count, lv, Lv.d_row_task_tc,
-                           Lv.d_cores, Lv.ld, Lv.tmap[tmi], H->d_grp_counter + lv, Lv.d_order[tmi]);
-                launches += 2;
-                continue;
-            }
-            launch_tc_pack_x(W[lv], (long long)H->nrc * Lv.pd, Lv.pd, Lv.nbox, nh, Rp, Lv.tc.kc,
-                             Lv.tc.nchunks, 0, d, n, H->leaf, L, nullptr, 0, Lv.d_Wp, s);
-            tc_launch(Lv.tc, Lv.tc_t0, Lv.tc_t1, Lv.d_far_col, Lv.d_far_core, Lv.d_cores, Lv.d_Wp,
-                      Lv.pd, Lv.ld);
+            launch_tcg_pack_x(W[lv], (long long)H->nrc * Lv.pd, Lv.pd, Lv.nbox, nh, Rpg,
+                              Lv.tg.nch, 0, d, n, H->leaf, L, nullptr, 0, Lv.d_Wg, s);
+            tcg_launch(Lv.tg, Lv.d_cls, Lv.cls_start, Lv.cls_count, lv, Lv.d_row_task_tc,
+                       Lv.d_cores, Lv.ld, Lv.tmap[tmi], H->d_grp_counter + lv, Lv.d_order[tmi]);
             launches += 2;
         }
-        if (H->near_prec == kPrecBF16X6 && H->near_tcg) {
+        if (H->near_prec == kPrecBF16X6) {
             launch_tcg_pack_x(nullptr, 0, H->near_rows, 1 << (d * L), nh, Rpg, H->near_tg.nch, 1,
                               d, n, H->leaf, L, uc, N, H->d_Ug, s);
             tcg_launch(H->near_tg, H->d_near_cls, H->near_cls_start, H->near_cls_count, L,
                        H->d_near_row_task_tc, H->d_near, H->near_ld, H->near_tmap[tmi],
                        H->d_grp_counter + L + 1, H->d_near_order[tmi]);
-            launches += 2;
-        } else if (H->near_prec == kPrecBF16X6) {
-            launch_tc_pack_x(nullptr, 0, H->near_rows, 1 << (d * L), nh, Rp, H->near_tc.kc,
-                             H->near_tc.nchunks, 1, d, n, H->leaf, L, uc, N, H->d_Up, s);
-            tc_launch(H->near_tc, H->near_tc_t0, H->near_tc_t1, H->d_near_col, H->d_near_blk,
-                      H->d_near, H->d_Up, H->near_rows, H->near_ld);
             launches += 2;
         }
     } else if (!H->tasks.empty()) {
@@ -1565,6 +1514,7 @@ int htlr_construct_ex(htlr_handle **out, const htlr_kernel *k, int d, int n, con
     int q = (o && o->quad_order > 0) ? o->quad_order : 16;
     if (q > 64) return fail(HTLR_EINVAL, "quad_order must be in 1..64");
     if (o && o->tc_segment < 0) return fail(HTLR_EINVAL, "tc_segment must be >= 0");
+    if (o && o->tc_flush < 0) return fail(HTLR_EINVAL, "tc_flush must be >= 0");
     if (o && o->tc_wait_cycles < 0) return fail(HTLR_EINVAL, "tc_wait_cycles must be >= 0");
     if (o && (o->orth < -1 || o->orth > 1)) return fail(HTLR_EINVAL, "orth must be -1, 0 or 1");
     if (o && (o->far_precision < 0 || o->far_precision > 3 || o->near_precision < 0 ||
@@ -1593,6 +1543,7 @@ int htlr_construct_ex(htlr_handle **out, const htlr_kernel *k, int d, int n, con
     H->far_prec = o ? o->far_precision : kPrecFP64;
     H->near_prec = o ? o->near_precision : kPrecFP64;
     if (o && o->tc_segment > 0) H->tc_seg_stages = o->tc_segment;
+    if (o && o->tc_flush > 0) H->tc_flush_segs = o->tc_flush;
     if (o && o->tc_wait_cycles > 0) H->tc_wait_cycles = o->tc_wait_cycles;
     int rc;
     try {
@@ -1738,22 +1689,17 @@ double htlr_tensor_flops(const htlr_handle *H, int nrhs)
                 for (int j = 0; j < nq; ++j) pairs += group_valid(d, nb1, G, b23, c1, j, cl, cs, cc);
         return (double)pairs * tg.nch * 6.0 * 2.0 * 128.0 * tg.Npad * 16.0;
     };
-    auto per_row = [&](const TcShape &ts, long long nblk, int Rp) {
-        return (double)nblk * ts.nchunks * (ts.kc / 16) * 6.0 * ts.mtiles * 2.0 * 128.0 * Rp * 16.0;
-    };
     for (int c0 = 0; c0 < nrhs; c0 += H->nrc) {
         const int nh = std::min(H->nrc, nrhs - c0);
-        const int Rp = (nh + 15) / 16 * 16, Rpg = nh <= 16 ? 16 : nh <= 32 ? 32 : 64;
+        const int Rpg = nh <= 16 ? 16 : nh <= 32 ? 32 : 64;
         for (int lv = 1; lv <= L; ++lv) {
             const LevelData &Lv = H->lev[lv];
             if (Lv.nfar == 0) continue;
-            total += Lv.tcg ? grouped(Lv.tg, Lv.h_cls, Lv.cls_start, Lv.cls_count, lv, Rpg)
-                            : per_row(Lv.tc, Lv.nfar, Rp);
+            total += grouped(Lv.tg, Lv.h_cls, Lv.cls_start, Lv.cls_count, lv, Rpg);
         }
         if (H->near_prec == kPrecBF16X6)
-            total += H->near_tcg ? grouped(H->near_tg, H->h_near_cls, H->near_cls_start,
-                                           H->near_cls_count, L, Rpg)
-                                 : per_row(H->near_tc, H->nnear, Rp);
+            total += grouped(H->near_tg, H->h_near_cls, H->near_cls_start, H->near_cls_count,
+                             L, Rpg);
     }
     return total;
 }

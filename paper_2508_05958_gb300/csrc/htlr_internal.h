@@ -69,18 +69,14 @@ struct KindDesc {
     long long x_box_stride;  // doubles per box in x (nrc * pd)
 };
 
-// Shape of a block list in the packed split-BF16 layout of the tensor-core stream.
 constexpr int kTcRpMax = 64;  // right-hand sides per tensor-core pass
-struct TcShape {
-    int rows = 0, cols = 0, mtiles = 0, kc = 0, nchunks = 0;
-    long long blk_elems = 0;     // bf16 elements per packed block
-    long long x_elems = 0;       // bf16 elements per packed source box (for kTcRpMax)
-};
 
 // Grouped tensor-core form of a SHARED block list (tc_group.cu): blocks Nd x Kd packed
 // as [chunk of 16 columns][split][row group][kcore][8][8], sources per box as
 // [split][chunk][row group][kcore][8][8]; the block rows (N) in `passes` passes of Nw
-// (Nw <= 256, so two accumulators of Nw columns fit in tensor memory).
+// (Nw <= kTcgMaxNw: two accumulators of Nw columns fit in tensor memory, and each drain
+// thread keeps Nw / 2 running sums in registers).
+constexpr int kTcgMaxNw = 256;
 struct TcgShape {
     int Kd = 0, Nd = 0, nch = 0, Npad = 0, NGb = 0, Nw = 0, passes = 0;
     long long core_elems = 0;    // bf16 elements per packed block
@@ -95,10 +91,7 @@ struct int4v {                    // (o1, o2, o3, block id) of a class offset li
 
 struct LevelData {
     int level = 0, nb = 0, nbox1 = 0, nbox = 0, pe = 0, pd = 0, ld = 0;
-    // tensor-core form (precision BF16X6)
-    TcShape tc;
-    uint16_t *d_Wp = nullptr;               // packed W, nbox x tc.x_elems
-    int tc_t0 = 0, tc_t1 = 0;               // task range in the tensor-core task list
+    // tensor-core form (precision BF16X6): partial slots per target row
     std::vector<int> row_task_tc;
     int *d_row_task_tc = nullptr;
     int64_t nfar = 0;
@@ -174,9 +167,6 @@ struct htlr_handle {
     std::vector<htlr::Task> tasks_tc;
     htlr::Task *d_tasks_tc = nullptr;
     double *d_part_tc = nullptr;
-    htlr::TcShape near_tc;
-    uint16_t *d_Up = nullptr;        // packed u per leaf
-    int near_tc_t0 = 0, near_tc_t1 = 0;
     int near_tcg = 0;                // grouped tensor-core path for the near field
     htlr::TcgShape near_tg;
     int near_cls_start[8] = {0}, near_cls_count[8] = {0};
@@ -198,7 +188,8 @@ struct htlr_handle {
     // changes whenever the device-side task tables are rebuilt (captured plans re-capture)
     size_t task_bytes = 256 * 1024;
     int stream_ctas_per_sm = 8, stream_threads = 256, tc_stages_cap = 0;
-    int tc_seg_stages = 8;   // grouped tensor-core kernel: K stages per FP32 accumulation
+    int tc_seg_stages = 4;   // grouped tensor-core kernel: K stages per TMEM segment
+    int tc_flush_segs = 32;  // grouped tensor-core kernel: segments per FP64 flush
     long long tc_wait_cycles = 4000000000ll;  // tensor-core kernels: bounded-wait limit
     int generation = 0;
     htlr_stats stats{};
@@ -350,11 +341,12 @@ struct TcgArgs {
     const int *row_task;
     double *part;
     int ld;
-    int stages, tmem_cols;
+    int stages, lead_stages, tmem_cols;  // cross and lead copy-ring depths
     int *err;
     int *counter;                      // next group (reset to 0 before each launch)
     const int *order;                  // groups, heaviest first
-    int seg_stages;                    // stages accumulated in TMEM before a drain to FP64
+    int seg_stages;                    // K stages per TMEM segment (fresh accumulator)
+    int flush_segs;                    // segments summed in FP32 before the FP64 flush
     long long wait_cycles;             // limit of each bounded wait (SM clock cycles)
 };
 void launch_tcg_pack_blocks(const double *src, long long nblk, int ld, int Nd, int Kd, int nch,
@@ -362,32 +354,14 @@ void launch_tcg_pack_blocks(const double *src, long long nblk, int ld, int Nd, i
 void launch_tcg_pack_x(const double *W, long long w_box_stride, int Kd, int nbox, int nr, int Rp,
                        int nch, int is_near, int d, int n, int leaf, int L, const double *u,
                        long long ldu, uint16_t *dst, cudaStream_t s);
-size_t tcg_stage_bytes(int NGw);
+// Shared-memory bytes of one slot of the lead ring (a1, b1) and of the cross ring (a2, a3,
+// b2, b3) of the grouped kernel for Nw = 8 NGw block rows per pass.
+size_t tcg_lead_bytes(int NGw);
+size_t tcg_cross_bytes(int NGw);
 void launch_tc_group(const TcgArgs &a, const void *tmap, cudaStream_t s);
 int tcg_encode_source_map(void *tmap_out, const uint16_t *base, int nch, int Rp, int nb1, int d);
-// ---- tc_stream.cu: tensor-core (tcgen05) block stream for many right-hand sides ----
-constexpr int kTcMaxStages = 8;
-struct TcArgs {
-    const Task *tasks;  // one task per non-empty block row
-    int t0, t1;
-    const int *col, *blk;      // CSR entries of the kind
-    const uint16_t *blocks;    // packed split-BF16 blocks
-    long long blk_elems;       // elements per packed block
-    const uint16_t *x;         // packed source operand, per source box
-    long long x_box_elems;
-    int mtiles, kc, nchunks, Rp, nr, rows, ld, stages, tmem_cols;
-    double *part;
-    int *err;
-    long long wait_cycles;     // limit of each bounded wait (SM clock cycles)
-};
-void launch_tc_stream(const TcArgs &a, cudaStream_t s);
-// Shared-memory bytes of one pipeline stage (A chunk + B chunk, all splits).
-size_t tc_stage_bytes(int mtiles, int kc, int Rp);
-void launch_tc_pack_blocks(const double *src, long long nblk, int ld, int rows, int cols,
-                           int mtiles, int kc, int nchunks, uint16_t *dst, cudaStream_t s);
-void launch_tc_pack_x(const double *W, long long w_box_stride, int pd, int nbox, int nr, int Rp,
-                      int kc, int nchunks, int is_near, int d, int n, int leaf, int L,
-                      const double *u, long long ldu, uint16_t *dst, cudaStream_t s);
+constexpr int kTcMaxStages = 8;   // deepest cross copy ring of the tensor-core kernel
+constexpr int kTcMaxLead = 16;    // deepest lead copy ring
 
 // Tensor grids: factors of every (level, dim, box), U(i, mu) = L_mu(x_i) and
 // V(i, mu) = L_mu(x_i) w_i on the Chebyshev points of the box's geometric cell.

@@ -33,8 +33,8 @@
 // 2e-8 relative per accumulated MMA, with a bias, so the error grows with the number of
 // MMAs summed in one accumulator (7.6e-4 over a whole c3 row).  Every `seg_stages`
 // stages the MMA thread commits the segment and switches to the other of two TMEM
-// accumulator buffers (N <= 256 columns each; wider block lists are done in two passes
-// over N).  The drain warps read the finished buffer with tcgen05.ld, add it to FP32
+// accumulator buffers (N <= 256 columns each; wider block lists are done in several
+// passes over N).  The drain warps read the finished buffer with tcgen05.ld, add it to FP32
 // sums held in their registers (two warps per TMEM lane quadrant, half the columns
 // each), and release the buffer.  The drain of one segment overlaps the MMAs of the
 // next.  At the end of a pass the sums are written as the FP64 partials of the group's
@@ -55,10 +55,31 @@ namespace {
 
 constexpr int kGThreads = 320;        // MMA warp, copy warp, eight drain warps
 constexpr int kDrainThreads = 256;
-constexpr int kMaxDrainChunks = 16;   // 8-column chunks per drain thread (Nw <= 256)
+constexpr int kMaxDrainChunks = kTcgMaxNw / 16;   // 8-column chunks per drain thread
+constexpr int kLdBatch = 1;           // tensor-memory loads in flight per drain thread
 constexpr int kMaxGroupOffsets = 1024;
 
 }  // namespace
+
+// FP32 -> FP64 by integer operations (the FP64 pipe is slow on this part); zero and
+// subnormal inputs give signed zero, infinities and NaN keep their class.
+__device__ __forceinline__ double widen_f32(float f)
+{
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t e = (b >> 23) & 0xFFu;
+    const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
+    const unsigned long long man = (unsigned long long)(b & 0x7FFFFFu) << 29;
+    unsigned long long bits = sign | ((unsigned long long)(e + 896u) << 52) | man;
+    bits = e == 0u ? sign : bits;
+    bits = e == 0xFFu ? (sign | 0x7FF0000000000000ull | man) : bits;
+    return __longlong_as_double((long long)bits);
+}
+
+// *p += v in FP64 at L2, without waiting for it (the owner thread is the only writer).
+__device__ __forceinline__ void red_add_f64(double *p, double v)
+{
+    asm volatile("red.global.add.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
 
 // ---------------------------------------------------------------------------------
 // Construction: pack FP64 blocks ([s][t], leading dimension ld, Nd x Kd) into
@@ -155,26 +176,34 @@ __global__ void __launch_bounds__(kGThreads, 1)
     tc_group_kernel(const __grid_constant__ CUtensorMap tmap, TcgArgs A)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
-    __shared__ uint64_t full_bar[kTcMaxStages], empty_bar[kTcMaxStages];
+    // two copy rings: the lead ring holds a1 and b1 of a stage until the segment's leading
+    // products are issued; the cross ring holds a2, a3, b2, b3 and is released as soon as
+    // the stage's cross products are done.  full_bar (per cross slot) completes when all
+    // of a stage's copies have landed
+    __shared__ uint64_t full_bar[kTcMaxStages], cross_empty[kTcMaxStages];
+    __shared__ uint64_t lead_empty[kTcMaxLead];
     __shared__ uint64_t seg_full[2], seg_empty[2], done_bar;
     __shared__ uint32_t tmem_holder, consumed;
     __shared__ volatile int abort_flag;
     __shared__ int n_valid, cur_group;
     __shared__ short valid_idx[kMaxGroupOffsets];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int S = A.stages, G = A.G, Rp = A.Rp, NGa = Rp / 8, nch = A.nch, NGb = A.NGb;
+    const int Sc = A.stages, Sl = A.lead_stages;
+    const int G = A.G, Rp = A.Rp, NGa = Rp / 8, nch = A.nch, NGb = A.NGb;
     const int Nw = A.Nw, NGw = Nw / 8, passes = A.passes;
     const long long F = A.seg_stages;                           // stages per segment
     const uint32_t a_split_bytes = 128u * 16u * 2u;             // 128 rows x 16 columns
-    const uint32_t a_bytes = kSplits * a_split_bytes;
     const uint32_t b_split_bytes = (uint32_t)NGw * 256u;        // Nw rows x 16 columns
-    const uint32_t b_bytes = kSplits * b_split_bytes;
-    const uint32_t stage_bytes = a_bytes + b_bytes;
+    const uint32_t lead_bytes = a_split_bytes + b_split_bytes;  // a1, b1
+    const uint32_t cross_bytes = 2u * lead_bytes;               // a2, a3, b2, b3
+    const uint32_t stage_bytes = lead_bytes + cross_bytes;
+    unsigned char *const cross_ring = sm + (size_t)Sl * lead_bytes;
     if (tid == 0) {
-        for (int s = 0; s < S; ++s) {
+        for (int s = 0; s < Sc; ++s) {
             mbar_init(&full_bar[s], 1);
-            mbar_init(&empty_bar[s], 1);
+            mbar_init(&cross_empty[s], 1);
         }
+        for (int s = 0; s < Sl; ++s) mbar_init(&lead_empty[s], 1);
         for (int b = 0; b < 2; ++b) {
             mbar_init(&seg_full[b], 1);
             mbar_init(&seg_empty[b], kDrainThreads);
@@ -198,7 +227,6 @@ __global__ void __launch_bounds__(kGThreads, 1)
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(Nw >> 3) << 17) |
                            ((uint32_t)(128 >> 4) << 24);
     const uint32_t lbo = 128, sbo = 256;
-    const int pa[6] = {0, 0, 1, 0, 1, 2}, pb[6] = {0, 1, 0, 2, 1, 0};
     const int nb1 = A.nb1;
     // drain warps 2..9: TMEM lane quadrant warp % 4 (accumulator row m), and one half of
     // the Nw columns of a pass each; their running sums stay in registers
@@ -210,6 +238,13 @@ __global__ void __launch_bounds__(kGThreads, 1)
     // counters run across groups
     uint32_t it_p = 0;       // loads issued (producer, tid 32)
     uint32_t it_c = 0;       // stages consumed (MMA thread, tid 0)
+    // ring positions, carried incrementally (no divisions in the issue loops): slot
+    // index, lap parity and "first lap" of the cross and lead rings, per role
+    int pc = 0, pl = 0;                      // producer: next cross / lead slot
+    uint32_t pc_lap = 0, pl_lap = 0;         // producer: lap parity of those slots
+    bool pc_first = true, pl_first = true;   // producer: slot not used before
+    int mc = 0, ml = 0;                      // MMA thread: next cross / lead slot
+    uint32_t mc_lap = 0;                     // MMA thread: lap parity of the cross slot
     uint32_t sc_m = 0;       // segments committed (MMA thread)
     uint32_t sc_d = 0;       // segments drained (drain threads)
     int done_pending = 0;
@@ -255,126 +290,220 @@ __global__ void __launch_bounds__(kGThreads, 1)
         const long long total = (long long)n_valid * nch;          // stages per pass
         const long long nseg = (total + F - 1) / F;                 // segments per pass
         if (tid == 32 && total > 0) {
-            // producer: refill a stage as soon as the MMAs that read it are done
-            for (int ps = 0; ps < passes && !abort_flag; ++ps)
+            // producer: stage it_p goes to cross slot it_p % Sc and lead slot it_p % Sl, each
+            // refilled once the MMAs that read its previous stage are done
+            for (int ps = 0; ps < passes && !abort_flag; ++ps) {
+                int oi = 0, ch = 0;                    // offset (in valid order) and chunk
                 for (long long q = 0; q < total; ++q, ++it_p) {
-                    const int s = (int)(it_p % S);
-                    if (it_p >= (uint32_t)S &&
-                        !mbar_wait(&empty_bar[s], ((it_p / S) - 1) & 1, A.wait_cycles, &abort_flag)) {
+                    const int c = pc, l = pl;
+                    if (!pc_first &&
+                        !mbar_wait(&cross_empty[c], pc_lap ^ 1u, A.wait_cycles, &abort_flag)) {
                         abort_flag = 1;
                         break;
                     }
-                    const int4 o = offs[valid_idx[(int)(q / nch)]];
-                    const int ch = (int)(q % nch);
+                    if (!pl_first &&
+                        !mbar_wait(&lead_empty[l], pl_lap ^ 1u, A.wait_cycles, &abort_flag)) {
+                        abort_flag = 1;
+                        break;
+                    }
+                    if (++pc == Sc) {
+                        pc = 0;
+                        pc_lap ^= 1u;
+                        pc_first = false;
+                    }
+                    if (++pl == Sl) {
+                        pl = 0;
+                        pl_lap ^= 1u;
+                        pl_first = false;
+                    }
+                    const int4 o = offs[valid_idx[oi]];
+                    const int chc = ch;
+                    if (++ch == nch) {
+                        ch = 0;
+                        ++oi;
+                    }
                     const int s0 = t0b1 + o.x;                 // b_1 of the first source
                     const int sc1 = s0 & 1;                    // (two's complement: also < 0)
                     const int sq0 = (s0 - sc1) / 2;
                     const int sb23 = (b2 + o.y) + nb1 * (b3 + o.z);
-                    unsigned char *st = sm + (size_t)s * stage_bytes;
+                    unsigned char *ld = sm + (size_t)l * lead_bytes;
+                    unsigned char *cr = cross_ring + (size_t)c * cross_bytes;
                     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
-                                     smem_u32(&full_bar[s])),
+                                     smem_u32(&full_bar[c])),
                                  "r"(stage_bytes)
                                  : "memory");
-                    for (int a = 0; a < kSplits; ++a)
-                        tensor_load_5d(st + a * a_split_bytes, &tmap, 0, (a * nch + ch) * NGa, sc1,
-                                       sq0, sb23, &full_bar[s]);
+                    // A splits: a1 to the lead slot, a2 and a3 to the cross slot
+                    tensor_load_5d(ld, &tmap, 0, chc * NGa, sc1, sq0, sb23, &full_bar[c]);
+                    for (int a = 1; a < kSplits; ++a)
+                        tensor_load_5d(cr + (a - 1) * a_split_bytes, &tmap, 0, (a * nch + chc) * NGa,
+                                       sc1, sq0, sb23, &full_bar[c]);
+                    // B splits (block B_o, chunk ch, this pass's rows): b1 to the lead slot, b2
+                    // and b3 to the cross slot (contiguous when the block is one pass wide)
                     const uint16_t *gb = A.blocks + (long long)o.w * A.core_elems +
-                                         (long long)ch * (kSplits * NGb * 128);
+                                         (long long)chc * (kSplits * NGb * 128) +
+                                         (long long)ps * NGw * 128;
+                    bulk_load(ld + a_split_bytes, gb, b_split_bytes, &full_bar[c]);
                     if (passes == 1) {
-                        bulk_load(st + a_bytes, gb, b_bytes, &full_bar[s]);
+                        bulk_load(cr + 2 * a_split_bytes, gb + (long long)NGb * 128,
+                                  2 * b_split_bytes, &full_bar[c]);
                     } else {
-                        for (int b = 0; b < kSplits; ++b)
-                            bulk_load(st + a_bytes + b * b_split_bytes,
-                                      gb + (long long)b * NGb * 128 + (long long)ps * NGw * 128,
-                                      b_split_bytes, &full_bar[s]);
+                        for (int b = 1; b < kSplits; ++b)
+                            bulk_load(cr + 2 * a_split_bytes + (b - 1) * b_split_bytes,
+                                      gb + (long long)b * NGb * 128, b_split_bytes, &full_bar[c]);
                     }
                 }
+            }
         }
         if (tid == 0 && total > 0) {
-            // MMA issue: the six split products into the segment's accumulator buffer
+            // MMA issue, segment by segment: a segment is F consecutive stages accumulated
+            // in one TMEM buffer, started fresh.  Each stage's cross products (a3b1, a2b2,
+            // a1b3, a2b1, a1b2) are issued as soon as it lands, and its cross slot released;
+            // the leading products a1b1 of the segment come last, once the accumulator holds
+            // the small cross terms only, so that its truncation acts on few additions of
+            // full magnitude
+            // shared-memory descriptors as a base plus (byte offset >> 4): the address field
+            // is the low 14 bits (addresses below 256 KB), so offsets add without carry
+            const uint64_t d0 = smem_desc(smem_u32(sm), lbo, sbo);
+            const uint32_t a16 = a_split_bytes >> 4, b16 = b_split_bytes >> 4;
+            const uint32_t lead16 = lead_bytes >> 4, cross16 = cross_bytes >> 4;
+            const uint32_t cring16 = (uint32_t)((size_t)Sl * lead_bytes) >> 4;
             for (int ps = 0; ps < passes && !abort_flag; ++ps)
-                for (long long q = 0; q < total; ++q, ++it_c) {
-                    const long long qs = q % F;
+                for (long long q0 = 0; q0 < total; q0 += F) {
+                    const int nq = (int)(total - q0 < F ? total - q0 : F);
                     const uint32_t buf = sc_m & 1;
-                    if (qs == 0) {
-                        // the buffer's previous segment must be drained before it is reset
-                        if (sc_m >= 2 &&
-                            !mbar_wait(&seg_empty[buf], ((sc_m >> 1) - 1) & 1, A.wait_cycles, &abort_flag)) {
-                            abort_flag = 1;
-                            break;
-                        }
-                        asm volatile("tcgen05.fence::after_thread_sync;");
-                    }
-                    const int s = (int)(it_c % S);
-                    if (!mbar_wait(&full_bar[s], (it_c / S) & 1, A.wait_cycles, &abort_flag)) {
-                        abort_flag = 1;
-                        break;
-                    }
-                    const uint32_t a_base = smem_u32(sm + (size_t)s * stage_bytes);
-                    const uint32_t b_base = a_base + a_bytes;
-                    for (int pr = 0; pr < 6; ++pr) {
-                        const uint32_t accumulate = (qs == 0 && pr == 0) ? 0u : 1u;
-                        mma_bf16(tmem + buf * (uint32_t)Nw,
-                                 smem_desc(a_base + pa[pr] * a_split_bytes, lbo, sbo),
-                                 smem_desc(b_base + pb[pr] * b_split_bytes, lbo, sbo), idesc,
-                                 accumulate);
-                    }
-                    mma_commit(&empty_bar[s]);
-                    if (qs == F - 1 || q == total - 1) {
-                        mma_commit(&seg_full[buf]);
-                        ++sc_m;
-                    }
-                }
-            consumed = it_c;
-        }
-        if (drainer) {
-            // accumulator row m = k Rp + r: target tau_k = tau_0 + 2k e_1, RHS r
-            const int k = m / Rp, r = m % Rp;
-            const int tb1 = t0b1 + 2 * k;
-            double *out = nullptr;
-            if (tb1 < nb1 && r < A.nr) {
-                const int tau = tb1 + nb1 * b23;
-                const int ta = A.row_task[tau];
-                if (A.row_task[tau + 1] > ta) out = A.part + A.tasks[ta].part + (long long)r * A.ld;
-            }
-            for (int ps = 0; ps < passes; ++ps) {
-                float acc[kMaxDrainChunks * 8];
-#pragma unroll
-                for (int i = 0; i < kMaxDrainChunks * 8; ++i) acc[i] = 0.f;
-                for (long long sg = 0; sg < nseg; ++sg, ++sc_d) {
-                    const uint32_t buf = sc_d & 1;
-                    if (!mbar_wait(&seg_full[buf], (sc_d >> 1) & 1, A.wait_cycles, &abort_flag)) {
+                    const uint32_t dt = tmem + buf * (uint32_t)Nw;
+                    // the buffer's previous segment must be drained before it is reset
+                    if (sc_m >= 2 &&
+                        !mbar_wait(&seg_empty[buf], ((sc_m >> 1) - 1) & 1, A.wait_cycles, &abort_flag)) {
                         abort_flag = 1;
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;");
-                    const uint32_t tbase = tmem + ((uint32_t)((warp & 3) * 32) << 16) +
-                                           buf * (uint32_t)Nw + (uint32_t)my_c0;
+                    const int ml0 = ml;                      // lead slot of the segment's first stage
+                    bool landed = true;
+                    for (int i = 0; i < nq; ++i) {
+                        if (!mbar_wait(&full_bar[mc], mc_lap, A.wait_cycles, &abort_flag)) {
+                            landed = false;
+                            break;
+                        }
+                        ++it_c;
+                        const uint64_t dl = d0 + (uint64_t)((uint32_t)ml * lead16);   // a1 | b1
+                        const uint64_t dc = d0 + (uint64_t)(cring16 + (uint32_t)mc * cross16);
+                        // a2 = dc, a3 = dc + a16, b2 = dc + 2 a16, b3 = dc + 2 a16 + b16;
+                        // a1 = dl, b1 = dl + a16
+                        mma_bf16(dt, dc + a16, dl + a16, idesc, i == 0 ? 0u : 1u);     // a3 b1
+                        mma_bf16(dt, dc, dc + 2 * a16, idesc, 1u);                      // a2 b2
+                        mma_bf16(dt, dl, dc + 2 * a16 + b16, idesc, 1u);                // a1 b3
+                        mma_bf16(dt, dc, dl + a16, idesc, 1u);                          // a2 b1
+                        mma_bf16(dt, dl, dc + 2 * a16, idesc, 1u);                      // a1 b2
+                        mma_commit(&cross_empty[mc]);
+                        if (++mc == Sc) {
+                            mc = 0;
+                            mc_lap ^= 1u;
+                        }
+                        if (++ml == Sl) ml = 0;
+                    }
+                    if (!landed) {
+                        abort_flag = 1;
+                        break;
+                    }
+                    for (int i = 0, l = ml0; i < nq; ++i) {
+                        const uint64_t dl = d0 + (uint64_t)((uint32_t)l * lead16);
+                        mma_bf16(dt, dl, dl + a16, idesc, 1u);                          // a1 b1
+                        mma_commit(&lead_empty[l]);
+                        if (++l == Sl) l = 0;
+                    }
+                    mma_commit(&seg_full[buf]);
+                    ++sc_m;
+                }
+            consumed = it_c;
+        }
+        if (drainer) {
+            // accumulator row m = k Rp + r: target tau_k = tau_0 + 2k e_1, RHS r.  Its FP64
+            // partial row in global memory, or null for padding rows (looked up again at each
+            // flush rather than held in registers through the drain loop)
+            auto row_out = [&]() -> double * {
+                const int k = m / Rp, r = m % Rp;
+                const int tb1 = t0b1 + 2 * k;
+                if (tb1 >= nb1 || r >= A.nr) return nullptr;
+                const int tau = tb1 + nb1 * b23;
+                const int ta = A.row_task[tau];
+                if (A.row_task[tau + 1] <= ta) return nullptr;
+                return A.part + A.tasks[ta].part + (long long)r * A.ld;
+            };
+            const int FL = A.flush_segs;
+            for (int ps = 0; ps < passes; ++ps) {
+                // FP32 sums of the drained segments; every FL segments (and after the last
+                // one) they go to the row's FP64 partial: stored by the first flush of the
+                // pass, then added by fire-and-forget L2 reductions, so the drain never waits
+                // on memory
+                for (long long g0 = 0; g0 < nseg && !abort_flag; g0 += FL) {
+                    const long long g1 = g0 + FL < nseg ? g0 + FL : nseg;
+                    float acc[kMaxDrainChunks * 8];
 #pragma unroll
-                    for (int c = 0; c < kMaxDrainChunks; ++c) {
-                        if (c < nck) {
-                            uint32_t v[8];
-                            asm volatile(
-                                "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]),
-                                  "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
-                                : "r"(tbase + (uint32_t)(8 * c)));
-                            asm volatile("tcgen05.wait::ld.sync.aligned;");
+                    for (int i = 0; i < kMaxDrainChunks * 8; ++i) acc[i] = 0.f;
+                    for (long long sg = g0; sg < g1; ++sg, ++sc_d) {
+                        const uint32_t buf = sc_d & 1;
+                        if (!mbar_wait(&seg_full[buf], (sc_d >> 1) & 1, A.wait_cycles, &abort_flag)) {
+                            abort_flag = 1;
+                            break;
+                        }
+                        asm volatile("tcgen05.fence::after_thread_sync;");
+                        const uint32_t tbase = tmem + ((uint32_t)((warp & 3) * 32) << 16) +
+                                               buf * (uint32_t)Nw + (uint32_t)my_c0;
+                        // kLdBatch 8-column loads in flight, then one wait
 #pragma unroll
-                            for (int jj = 0; jj < 8; ++jj) acc[8 * c + jj] += __uint_as_float(v[jj]);
+                        for (int c0 = 0; c0 < kMaxDrainChunks; c0 += kLdBatch) {
+                            if (c0 < nck) {
+                                uint32_t v[kLdBatch][8];
+#pragma unroll
+                                for (int cc = 0; cc < kLdBatch; ++cc)
+                                    if (c0 + cc < nck)
+                                        asm volatile(
+                                            "tcgen05.ld.sync.aligned.32x32b.x8.b32 "
+                                            "{%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                                            : "=r"(v[cc][0]), "=r"(v[cc][1]), "=r"(v[cc][2]),
+                                              "=r"(v[cc][3]), "=r"(v[cc][4]), "=r"(v[cc][5]),
+                                              "=r"(v[cc][6]), "=r"(v[cc][7])
+                                            : "r"(tbase + (uint32_t)(8 * (c0 + cc))));
+                                asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+                                for (int cc = 0; cc < kLdBatch; ++cc)
+                                    if (c0 + cc < nck)
+#pragma unroll
+                                        for (int jj = 0; jj < 8; ++jj)
+                                            acc[8 * (c0 + cc) + jj] += __uint_as_float(v[cc][jj]);
+                            }
+                        }
+                        asm volatile("tcgen05.fence::before_thread_sync;");
+                        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(
+                                         smem_u32(&seg_empty[buf]))
+                                     : "memory");
+                    }
+                    if (abort_flag) break;
+                    double *o = row_out();
+                    if (o) {
+                        const int col0 = ps * Nw + my_c0;
+                        const int lim = min(my_cols, A.Nd - col0);
+                        o += col0;
+                        if (g0 > 0) {
+#pragma unroll
+                            for (int i = 0; i < kMaxDrainChunks * 8; ++i)
+                                if (i < lim) red_add_f64(o + i, widen_f32(acc[i]));
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < kMaxDrainChunks * 8; ++i)
+                                if (i < lim) o[i] = widen_f32(acc[i]);
                         }
                     }
-                    asm volatile("tcgen05.fence::before_thread_sync;");
-                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(
-                                     smem_u32(&seg_empty[buf]))
-                                 : "memory");
                 }
                 if (abort_flag) break;
-                if (out) {
+                double *o = row_out();
+                if (nseg == 0 && o) {
+                    // a pass without segments: the row's partial is zero
                     const int col0 = ps * Nw + my_c0;
-#pragma unroll
-                    for (int i = 0; i < kMaxDrainChunks * 8; ++i)
-                        if (i < my_cols && col0 + i < A.Nd) out[col0 + i] = (double)acc[i];
+                    for (int i = 0; i < my_cols; ++i)
+                        if (col0 + i < A.Nd) o[col0 + i] = 0.0;
                 }
             }
         }
@@ -398,7 +527,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
         if (tid == 32) {
             // every copy issued into shared memory lands before the CTA exits
             for (uint32_t it = consumed; it < it_p; ++it)
-                mbar_wait(&full_bar[it % S], (it / S) & 1);
+                mbar_wait(&full_bar[it % Sc], (it / Sc) & 1);
         }
         __syncthreads();
     }
@@ -409,13 +538,14 @@ __global__ void __launch_bounds__(kGThreads, 1)
                      "r"(A.tmem_cols));
 }
 
-size_t tcg_stage_bytes(int NGw) { return (size_t)kSplits * 128 * 16 * 2 + (size_t)kSplits * NGw * 256; }
+size_t tcg_lead_bytes(int NGw) { return (size_t)128 * 16 * 2 + (size_t)NGw * 256; }
+size_t tcg_cross_bytes(int NGw) { return 2 * tcg_lead_bytes(NGw); }
 
 void launch_tc_group(const TcgArgs &a, const void *tmap, cudaStream_t s)
 {
     if (a.ngroups <= 0) return;
     cudaMemsetAsync(a.counter, 0, sizeof(int), s);
-    const size_t smem = tcg_stage_bytes(a.Nw / 8) * a.stages;
+    const size_t smem = tcg_lead_bytes(a.Nw / 8) * a.lead_stages + tcg_cross_bytes(a.Nw / 8) * a.stages;
     cudaFuncSetAttribute(tc_group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int grid = a.ngroups < 152 ? (int)a.ngroups : 152;
     tc_group_kernel<<<grid, kGThreads, smem, s>>>(*static_cast<const CUtensorMap *>(tmap), a);

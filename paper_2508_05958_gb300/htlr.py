@@ -51,7 +51,8 @@ class htlr_options(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int), ("orth", ctypes.c_int), ("quad_order", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("hbm_limit", ctypes.c_size_t),
                 ("far_precision", ctypes.c_int), ("near_precision", ctypes.c_int),
-                ("tc_segment", ctypes.c_int), ("tc_wait_cycles", ctypes.c_longlong)]
+                ("tc_segment", ctypes.c_int), ("tc_flush", ctypes.c_int),
+                ("tc_wait_cycles", ctypes.c_longlong)]
 
 
 class htlr_stats(ctypes.Structure):
@@ -235,7 +236,8 @@ def _hptr(a):
 
 def htlr_construct(ktype, d, n, leaf, r, eta, *, kscale=1.0, kparam=0.0, a=None, grid=None,
                    storage=STORE_AUTO, orth=-1, quad_order=0, stream=None, hbm_limit=0,
-                   far_precision=0, near_precision=0, tc_segment=0, tc_wait_cycles=0):
+                   far_precision=0, near_precision=0, tc_segment=0, tc_flush=0,
+                   tc_wait_cycles=0):
     """Construct (Algorithm 1).  ``a``: host array of N values (natural order) or None.
     ``grid``: None (uniform) or (coords (d, n), edges (d, n+1)).  Returns an opaque handle
     (int).  ``stream``: a torch.cuda.Stream, a raw cudaStream_t int, or None."""
@@ -256,7 +258,7 @@ def htlr_construct(ktype, d, n, leaf, r, eta, *, kscale=1.0, kparam=0.0, a=None,
         keep.append(a)
         g.a = _hptr(a)
     o = htlr_options(storage, orth, quad_order, _stream_ptr(stream), hbm_limit, far_precision,
-                     near_precision, tc_segment, tc_wait_cycles)
+                     near_precision, tc_segment, tc_flush, tc_wait_cycles)
     h = ctypes.c_void_p()
     _check(L.htlr_construct_ex(ctypes.byref(h), ctypes.byref(k), d, n, ctypes.byref(g), leaf, r,
                                eta, ctypes.byref(o)))

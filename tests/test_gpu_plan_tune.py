@@ -167,7 +167,7 @@ def test_autotune_tensor_core_ring_depth(oracle):
     w = workload("c1")
     htlr.htlr_autotune_clear_cache()
     u = w.u(nrhs=8)
-    H = _construct(w, storage=1, far_precision=3, near_precision=3)
+    H = _construct(w, storage=2, far_precision=3, near_precision=3)
     try:
         ud = _dev(u)
         f0 = torch.empty_like(ud)
