@@ -15,6 +15,72 @@
 
 namespace htlr {
 
+// Arithmetic of the up and out contractions.  ArithFP64: plain FP64 FMAs (the FP64 mode).
+// ArithDF64: float pairs (hi, lo) with hi + lo equal to the FP64 value to 2^-48, products
+// formed with the exact FMA error term and the two cross terms, sums by TwoSum, all on the
+// FP32 pipe; used with the df64, FP32 and BF16X6 far fields, whose own arithmetic is no
+// more accurate.  Both hold 8 bytes per value, so the shared-memory layouts agree.
+struct ArithFP64 {
+    using T = double;
+    static __device__ __forceinline__ T from(double x) { return x; }
+    static __device__ __forceinline__ double to(T a) { return a; }
+    static __device__ __forceinline__ T zero() { return 0.0; }
+    static __device__ __forceinline__ T mac(T a, T b, T acc) { return fma(a, b, acc); }
+    static __device__ __forceinline__ T add(T a, T b) { return a + b; }
+};
+
+struct ArithDF64 {
+    using T = float2;  // (hi, lo)
+    // FP64 -> (hi, lo) by integer operations (no FP64 instructions): hi keeps the sign,
+    // the exponent and the leading 24 bits of the significand, lo the next 24 of the
+    // remaining 29 (relative error below 2^-48).  |x| below 2^-100 gives zero, which is
+    // far under the operands of the product.
+    static __device__ __forceinline__ T from(double x)
+    {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+        const uint32_t e = (uint32_t)(b >> 52) & 0x7FFu;
+        const uint32_t sgn = (uint32_t)(b >> 32) & 0x80000000u;
+        if (e < 1023u - 100u) return make_float2(0.f, 0.f);
+        const float hi = __uint_as_float(sgn | ((e - 896u) << 23) | (uint32_t)((b >> 29) & 0x7FFFFFu));
+        // remainder r 2^(e - 1075), r < 2^29: as a float, normalised by its leading bit
+        const uint32_t r = (uint32_t)(b & 0x1FFFFFFFu);
+        if (r == 0u) return make_float2(hi, 0.f);
+        const int lz = __clz(r);                  // r < 2^29: lz >= 3
+        const int top = 31 - lz;                  // index of the leading bit of r
+        // significand: the 23 bits below the leading one (truncated)
+        const uint32_t man = top >= 23 ? (r >> (top - 23)) & 0x7FFFFFu : (r << (23 - top)) & 0x7FFFFFu;
+        const int ex = (int)e - 1075 + top + 127; // biased exponent of r 2^(e - 1075)
+        const float lo = ex > 0 ? __uint_as_float(sgn | ((uint32_t)ex << 23) | man) : 0.f;
+        return make_float2(hi, lo);
+    }
+    static __device__ __forceinline__ double to(T a) { return (double)a.x + (double)a.y; }
+    static __device__ __forceinline__ T zero() { return make_float2(0.f, 0.f); }
+    // acc + a b, renormalised (|lo| <= ulp(hi) / 2).  The _rn intrinsics keep the compiler
+    // from contracting the error-free transformations.
+    static __device__ __forceinline__ T mac(T a, T b, T acc)
+    {
+        const float p = __fmul_rn(a.x, b.x);
+        float e = __fmaf_rn(a.x, b.x, -p);          // a.hi b.hi - p, exactly
+        e = __fmaf_rn(a.x, b.y, e);
+        e = __fmaf_rn(a.y, b.x, e);
+        const float t = __fadd_rn(acc.x, p);        // TwoSum(acc.hi, p)
+        const float z = __fsub_rn(t, acc.x);
+        const float err = __fadd_rn(__fsub_rn(acc.x, __fsub_rn(t, z)), __fsub_rn(p, z));
+        const float lo = __fadd_rn(acc.y, __fadd_rn(err, e));
+        const float hi = __fadd_rn(t, lo);          // renormalise
+        return make_float2(hi, __fsub_rn(lo, __fsub_rn(hi, t)));
+    }
+    static __device__ __forceinline__ T add(T a, T b)
+    {
+        const float t = __fadd_rn(a.x, b.x);
+        const float z = __fsub_rn(t, a.x);
+        const float err = __fadd_rn(__fsub_rn(a.x, __fsub_rn(t, z)), __fsub_rn(b.x, z));
+        const float lo = __fadd_rn(__fadd_rn(a.y, b.y), err);
+        const float hi = __fadd_rn(t, lo);
+        return make_float2(hi, __fsub_rn(lo, __fsub_rn(hi, t)));
+    }
+};
+
 struct BoxDims {
     int first[3], cnt[3];
     const double *U[3], *V[3];
@@ -44,34 +110,44 @@ __device__ __forceinline__ BoxDims box_dims(const LevelGeom &g, int d, int box)
 // up: one CTA per (box, rhs).  Mode products in the order 1, 2, (3), slab by slab of
 // the last dimension so that shared memory stays bounded for large boxes.
 // ---------------------------------------------------------------------------------
+template <class AR>
 __global__ void __launch_bounds__(128) up_kernel(int d, int n, LevelGeom g,
                                                  const double *__restrict__ u, long long ldu,
                                                  int nrc, double *__restrict__ W, int slab)
 {
-    extern __shared__ double sm[];
+    using T = typename AR::T;
+    extern __shared__ __align__(16) unsigned char up_sm[];
+    T *sm = reinterpret_cast<T *>(up_sm);
     const int box = blockIdx.x, r = blockIdx.y;
     const int pe = g.pe, mc = g.maxcnt;
     const BoxDims b = box_dims(g, d, box);
     const double *ur = u + ldu * r;
-    double *Vs = sm;                      // d factors, mc x pe each (leading dim cnt_k)
-    double *Y1 = Vs + 3 * mc * pe;        // pe x c2 x slab
-    double *Y2 = Y1 + pe * mc * slab;     // pe x pe x c3
+    T *Vs = sm;                           // d factors, mc x pe each (leading dim cnt_k)
+    T *Y1 = Vs + 3 * mc * pe;             // pe x c2 x slab
+    T *Y2 = Y1 + pe * mc * slab;          // pe x pe x c3
+    T *Us = Y2 + pe * pe * mc;            // the slab of u_sigma, c1 x c2 x slab, converted once
     for (int k = 0; k < d; ++k)
-        for (int i = threadIdx.x; i < b.cnt[k] * pe; i += blockDim.x) Vs[k * mc * pe + i] = b.V[k][i];
+        for (int i = threadIdx.x; i < b.cnt[k] * pe; i += blockDim.x)
+            Vs[k * mc * pe + i] = AR::from(b.V[k][i]);
     __syncthreads();
     const int c1 = b.cnt[0], c2 = b.cnt[1], c3 = (d == 3) ? b.cnt[2] : 1;
-    const double *V1 = Vs, *V2 = Vs + mc * pe, *V3 = Vs + 2 * mc * pe;
+    const T *V1 = Vs, *V2 = Vs + mc * pe, *V3 = Vs + 2 * mc * pe;
     const long long base = (long long)b.first[0] + (long long)n * b.first[1] +
                            (d == 3 ? (long long)n * n * b.first[2] : 0);
     for (int i3g = 0; i3g < c3; i3g += slab) {
         const int ns = min(slab, c3 - i3g);
+        for (int idx = threadIdx.x; idx < c1 * c2 * ns; idx += blockDim.x) {
+            const int i1 = idx % c1, rest = idx / c1;
+            const int i2 = rest % c2, j3 = rest / c2;
+            Us[idx] = AR::from(ur[base + i1 + (long long)n * i2 + (long long)n * n * (i3g + j3)]);
+        }
+        __syncthreads();
         // mode 1: Y1[mu1 + pe (i2 + c2 j3)] = sum_i1 V1[i1, mu1] u[i1, i2, i3]
         for (int idx = threadIdx.x; idx < pe * c2 * ns; idx += blockDim.x) {
             int mu1 = idx % pe, rest = idx / pe;
-            int i2 = rest % c2, j3 = rest / c2;
-            const double *row = ur + base + (long long)n * i2 + (long long)n * n * (i3g + j3);
-            double acc = 0.0;
-            for (int i1 = 0; i1 < c1; ++i1) acc = fma(V1[i1 + c1 * mu1], row[i1], acc);
+            const T *row = Us + c1 * rest;
+            T acc = AR::zero();
+            for (int i1 = 0; i1 < c1; ++i1) acc = AR::mac(V1[i1 + c1 * mu1], row[i1], acc);
             Y1[idx] = acc;
         }
         __syncthreads();
@@ -79,9 +155,9 @@ __global__ void __launch_bounds__(128) up_kernel(int d, int n, LevelGeom g,
         for (int idx = threadIdx.x; idx < pe * pe * ns; idx += blockDim.x) {
             int mu1 = idx % pe, rest = idx / pe;
             int mu2 = rest % pe, j3 = rest / pe;
-            double acc = 0.0;
+            T acc = AR::zero();
             for (int i2 = 0; i2 < c2; ++i2)
-                acc = fma(V2[i2 + c2 * mu2], Y1[mu1 + pe * (i2 + c2 * j3)], acc);
+                acc = AR::mac(V2[i2 + c2 * mu2], Y1[mu1 + pe * (i2 + c2 * j3)], acc);
             Y2[mu1 + pe * (mu2 + pe * (i3g + j3))] = acc;
         }
         __syncthreads();
@@ -89,33 +165,42 @@ __global__ void __launch_bounds__(128) up_kernel(int d, int n, LevelGeom g,
     const int pd = g.pd;
     double *Wout = W + ((long long)box * nrc + r) * pd;
     if (d == 2) {
-        for (int idx = threadIdx.x; idx < pd; idx += blockDim.x) Wout[idx] = Y2[idx];
+        for (int idx = threadIdx.x; idx < pd; idx += blockDim.x) Wout[idx] = AR::to(Y2[idx]);
         return;
     }
     // mode 3: W[mu1 + pe (mu2 + pe mu3)] = sum_i3 V3[i3, mu3] Y2[mu1 + pe (mu2 + pe i3)]
     for (int idx = threadIdx.x; idx < pd; idx += blockDim.x) {
         int m12 = idx % (pe * pe), mu3 = idx / (pe * pe);
-        double acc = 0.0;
-        for (int i3 = 0; i3 < c3; ++i3) acc = fma(V3[i3 + c3 * mu3], Y2[m12 + pe * pe * i3], acc);
-        Wout[idx] = acc;
+        T acc = AR::zero();
+        for (int i3 = 0; i3 < c3; ++i3) acc = AR::mac(V3[i3 + c3 * mu3], Y2[m12 + pe * pe * i3], acc);
+        Wout[idx] = AR::to(acc);
     }
 }
 
 void launch_up(int d, int n, const LevelGeom &g, const double *u, int nrhs_here, long long ldu,
-               int nrc, double *d_W, cudaStream_t s)
+               int nrc, double *d_W, cudaStream_t s, bool df64)
 {
     const int nbox = 1 << (d * g.level);
     const int mc = g.maxcnt, pe = g.pe;
     const int n3 = (d == 3) ? mc : 1;
-    // slab of the last dimension so that the mode-1 buffer stays within 64 KB
+    // slab of the last dimension so that the staged u and the mode-1 buffer stay within
+    // 64 KB
     int slab = n3;
-    while (slab > 1 && (long long)pe * mc * slab > 8192) slab = (slab + 1) / 2;
+    while (slab > 1 && (long long)(pe + mc) * mc * slab > 8192) slab = (slab + 1) / 2;
     size_t smem = sizeof(double) * ((size_t)3 * mc * pe + (size_t)pe * mc * slab +
-                                    (size_t)pe * pe * n3);
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(up_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                                    (size_t)pe * pe * mc + (size_t)mc * mc * slab);
     dim3 grid(nbox, nrhs_here);
-    up_kernel<<<grid, 128, smem, s>>>(d, n, g, u, ldu, nrc, d_W, slab);
+    if (df64) {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(up_kernel<ArithDF64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        up_kernel<ArithDF64><<<grid, 128, smem, s>>>(d, n, g, u, ldu, nrc, d_W, slab);
+    } else {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(up_kernel<ArithFP64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        up_kernel<ArithFP64><<<grid, 128, smem, s>>>(d, n, g, u, ldu, nrc, d_W, slab);
+    }
 }
 
 // The block stream (the hot loop) lives in stream_impl.cuh, instantiated per
@@ -176,19 +261,24 @@ void launch_reduce_far(int nbox, int pd, int ld, int nrc, int nrhs_here, const i
 // ---------------------------------------------------------------------------------
 constexpr int kOutPer = 8;  // rows per thread: leaves of up to 8 * 256 points
 
+template <class AR>
 __global__ void __launch_bounds__(256) out_kernel(OutArgs A)
 {
-    extern __shared__ double sm[];
+    using T = typename AR::T;
+    extern __shared__ __align__(16) unsigned char out_sm[];
+    T *sm = reinterpret_cast<T *>(out_sm);
     const int tau = blockIdx.x, r = blockIdx.y, d = A.d, n = A.n, L = A.L;
     const BoxDims lb = box_dims(A.leafg, d, tau);
     int t3[3] = {0, 0, 0};
     for (int k = 0; k < d; ++k) t3[k] = (tau >> (L * k)) & ((1 << L) - 1);
     const int rows = lb.cnt[0] * lb.cnt[1] * lb.cnt[2];
     const int per = (rows + blockDim.x - 1) / blockDim.x;
-    double acc[kOutPer];
+    double base[kOutPer];        // near field (+ a u + diagonal), FP64
+    T far[kOutPer];              // far field of all levels, in the arithmetic AR
     long long nat[kOutPer];
     for (int m = 0; m < kOutPer; ++m) {
-        acc[m] = 0.0;
+        base[m] = 0.0;
+        far[m] = AR::zero();
         nat[m] = -1;
         const int i = threadIdx.x + blockDim.x * m;
         if (m < per && i < rows) {
@@ -197,18 +287,19 @@ __global__ void __launch_bounds__(256) out_kernel(OutArgs A)
             const long long na = (long long)(lb.first[0] + j1) + (long long)n * (lb.first[1] + j2) +
                                  (d == 3 ? (long long)n * n * (lb.first[2] + j3) : 0);
             nat[m] = na;
-            double s = 0.0;
+            double sb = 0.0;
             if (A.near_in_f) {
-                s = A.f[na + A.ldf * r];
+                sb = A.f[na + A.ldf * r];
             } else {
                 for (int k = A.near_row_task[tau]; k < A.near_row_task[tau + 1]; ++k)
-                    s += A.part[A.tasks[k].part + (long long)r * A.near_ld + i];
-                if (A.a_add) s += A.a_add[na] * A.u[na + A.ldu * r];
-                if (A.diag_add) s += A.diag_add[na] * A.u[na + A.ldu * r];
+                    sb += A.part[A.tasks[k].part + (long long)r * A.near_ld + i];
+                if (A.a_add) sb += A.a_add[na] * A.u[na + A.ldu * r];
+                if (A.diag_add) sb += A.diag_add[na] * A.u[na + A.ldu * r];
             }
-            acc[m] = s;
+            base[m] = sb;
         }
     }
+    const int c1 = lb.cnt[0], c2 = lb.cnt[1], c3 = lb.cnt[2];
     for (int q = 0; q < A.ndown; ++q) {
         const DownLevel &D = A.down[q];
         const int pe = D.g.pe, lev = D.g.level;
@@ -217,70 +308,84 @@ __global__ void __launch_bounds__(256) out_kernel(OutArgs A)
         const BoxDims ab = box_dims(D.g, d, anc);
         int o[3];
         for (int k = 0; k < 3; ++k) o[k] = lb.first[k] - ab.first[k];
-        const int c1 = lb.cnt[0], c2 = lb.cnt[1], c3 = lb.cnt[2];
-        const int ca1 = ab.cnt[0], ca2 = ab.cnt[1], ca3 = ab.cnt[2];
         const double *Hb = D.H + ((long long)anc * A.nrc + r) * D.g.pd;
-        double *Hs = sm;                          // pd
-        double *Z3 = Hs + D.g.pd;                 // pe^2 * c3
-        double *Z2 = Z3 + pe * pe * c3;           // pe * c2 * c3
-        for (int i = threadIdx.x; i < D.g.pd; i += blockDim.x) Hs[i] = Hb[i];
+        T *Hs = sm;                               // pd
+        T *Z3 = Hs + D.g.pd;                      // pe^2 * c3
+        T *Z2 = Z3 + pe * pe * c3;                // pe * c2 * c3
+        T *Us = Z2 + pe * c2 * c3;                // the ancestor's factors on the leaf's rows
+        T *U1 = Us, *U2 = Us + c1 * pe, *U3 = U2 + c2 * pe;
+        for (int i = threadIdx.x; i < D.g.pd; i += blockDim.x) Hs[i] = AR::from(Hb[i]);
+        for (int i = threadIdx.x; i < c1 * pe; i += blockDim.x)
+            U1[i] = AR::from(ab.U[0][o[0] + i % c1 + ab.cnt[0] * (i / c1)]);
+        for (int i = threadIdx.x; i < c2 * pe; i += blockDim.x)
+            U2[i] = AR::from(ab.U[1][o[1] + i % c2 + ab.cnt[1] * (i / c2)]);
+        if (d == 3)
+            for (int i = threadIdx.x; i < c3 * pe; i += blockDim.x)
+                U3[i] = AR::from(ab.U[2][o[2] + i % c3 + ab.cnt[2] * (i / c3)]);
         __syncthreads();
-        const double *Zsrc = Hs;
+        const T *Zsrc = Hs;
         if (d == 3) {
-            // Z3[mu1 + pe (mu2 + pe j3)] = sum_mu3 U3[o3 + j3, mu3] H[mu1 + pe (mu2 + pe mu3)]
+            // Z3[mu1 + pe (mu2 + pe j3)] = sum_mu3 U3[j3, mu3] H[mu1 + pe (mu2 + pe mu3)]
             for (int idx = threadIdx.x; idx < pe * pe * c3; idx += blockDim.x) {
                 int m12 = idx % (pe * pe), j3 = idx / (pe * pe);
-                double s = 0.0;
+                T acc = AR::zero();
                 for (int m3 = 0; m3 < pe; ++m3)
-                    s = fma(ab.U[2][o[2] + j3 + ca3 * m3], Hs[m12 + pe * pe * m3], s);
-                Z3[idx] = s;
+                    acc = AR::mac(U3[j3 + c3 * m3], Hs[m12 + pe * pe * m3], acc);
+                Z3[idx] = acc;
             }
             __syncthreads();
             Zsrc = Z3;
         }
-        // Z2[mu1 + pe (j2 + c2 j3)] = sum_mu2 U2[o2 + j2, mu2] Zsrc[mu1 + pe (mu2 + pe j3)]
+        // Z2[mu1 + pe (j2 + c2 j3)] = sum_mu2 U2[j2, mu2] Zsrc[mu1 + pe (mu2 + pe j3)]
         for (int idx = threadIdx.x; idx < pe * c2 * c3; idx += blockDim.x) {
             int mu1 = idx % pe, rest = idx / pe;
             int j2 = rest % c2, j3 = rest / c2;
-            double s = 0.0;
+            T acc = AR::zero();
             for (int m2 = 0; m2 < pe; ++m2)
-                s = fma(ab.U[1][o[1] + j2 + ca2 * m2], Zsrc[mu1 + pe * (m2 + pe * j3)], s);
-            Z2[idx] = s;
+                acc = AR::mac(U2[j2 + c2 * m2], Zsrc[mu1 + pe * (m2 + pe * j3)], acc);
+            Z2[idx] = acc;
         }
         __syncthreads();
         for (int m = 0; m < kOutPer; ++m) {
             const int i = threadIdx.x + blockDim.x * m;
             if (m < per && i < rows) {
                 int j1 = i % c1, j23 = i / c1;
-                double s = 0.0;
-                for (int m1 = 0; m1 < pe; ++m1)
-                    s = fma(ab.U[0][o[0] + j1 + ca1 * m1], Z2[m1 + pe * j23], s);
-                acc[m] += s;
+                T acc = far[m];
+                for (int m1 = 0; m1 < pe; ++m1) acc = AR::mac(U1[j1 + c1 * m1], Z2[m1 + pe * j23], acc);
+                far[m] = acc;
             }
         }
         __syncthreads();
     }
     for (int m = 0; m < kOutPer; ++m)
-        if (nat[m] >= 0) A.f[nat[m] + A.ldf * r] = acc[m];
+        if (nat[m] >= 0) A.f[nat[m] + A.ldf * r] = base[m] + AR::to(far[m]);
 }
 
-void launch_out(const OutArgs &a, int max_rows, cudaStream_t s)
+void launch_out(const OutArgs &a, int max_rows, cudaStream_t s, bool df64)
 {
     size_t smem = 0;
     const int mcl = a.leafg.maxcnt > 1 ? a.leafg.maxcnt : 1;  // largest leaf extent
     for (int q = 0; q < a.ndown; ++q) {
         const int pe = a.down[q].g.pe;
         size_t need = (size_t)a.down[q].g.pd + (size_t)pe * pe * (a.d == 3 ? mcl : 1) +
-                      (size_t)pe * mcl * (a.d == 3 ? mcl : 1);
+                      (size_t)pe * mcl * (a.d == 3 ? mcl : 1) + (size_t)3 * mcl * pe;
         if (need > smem) smem = need;
     }
     smem *= sizeof(double);
     if (smem == 0) smem = sizeof(double);
     int threads = max_rows < 256 ? ((max_rows + 31) / 32) * 32 : 256;
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(out_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 grid(1 << (a.d * a.L), a.nrhs);
-    out_kernel<<<grid, threads, smem, s>>>(a);
+    if (df64) {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(out_kernel<ArithDF64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        out_kernel<ArithDF64><<<grid, threads, smem, s>>>(a);
+    } else {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(out_kernel<ArithFP64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        out_kernel<ArithFP64><<<grid, threads, smem, s>>>(a);
+    }
 }
 
 }  // namespace htlr

@@ -1240,7 +1240,7 @@ int run_chunk(const htlr_handle *H, const KindDesc *d_kinds, double *part,
     mark(0);
     for (int lv = 1; lv <= L; ++lv) {
         if (H->lev[lv].nfar == 0) continue;
-        launch_up(d, n, level_geom(H, lv), uc, nh, N, H->nrc, W[lv], s);
+        launch_up(d, n, level_geom(H, lv), uc, nh, N, H->nrc, W[lv], s, H->far_prec != kPrecFP64);
         ++launches;
     }
     mark(1);
@@ -1377,7 +1377,7 @@ int run_chunk(const htlr_handle *H, const KindDesc *d_kinds, double *part,
     }
     oa.f = fc;
     oa.ldf = N;
-    launch_out(oa, H->max_leaf_rows, s);
+    launch_out(oa, H->max_leaf_rows, s, H->far_prec != kPrecFP64);
     ++launches;
     mark(9);
     if (tev)

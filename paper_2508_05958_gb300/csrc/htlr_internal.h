@@ -284,8 +284,9 @@ struct DownLevel {
     LevelGeom g;
     const double *H;
 };
+// df64: float-pair arithmetic on the FP32 pipe (used unless the far field is FP64).
 void launch_up(int d, int n, const LevelGeom &g, const double *u, int nrhs_here, long long ldu,
-               int nrc, double *d_W, cudaStream_t s);
+               int nrc, double *d_W, cudaStream_t s, bool df64);
 // out: f_tau = base + sum over far levels of H_anc x_l U_l (rows of the leaf).  The base
 // is the sum of the leaf's dense-block task partials [+ a u] (near_in_f = 0), or the
 // value already in f written by the generated near field (near_in_f = 1).
@@ -306,7 +307,7 @@ struct OutArgs {
     double *f;
     long long ldf;
 };
-void launch_out(const OutArgs &a, int max_rows, cudaStream_t s);
+void launch_out(const OutArgs &a, int max_rows, cudaStream_t s, bool df64);
 // Generated near field: f_tau = sum over the leaf's near list of K(x_i, y_j) w_j u_j (j != i)
 // + (diag_i + a_i) u_i, kernel values recomputed in every call.  prec: kPrecFP64 or
 // kPrecFP32 (coordinates taken relative to the target leaf before rounding).
