@@ -75,10 +75,26 @@ __device__ __forceinline__ double widen_f32(float f)
     return __longlong_as_double((long long)bits);
 }
 
-// *p += v in FP64 at L2, without waiting for it (the owner thread is the only writer).
-__device__ __forceinline__ void red_add_f64(double *p, double v)
+// L2 policy for the partial rows: kept in L2 ahead of streamed data, so that the
+// periodic additions of a row find it there instead of in DRAM.
+__device__ __forceinline__ uint64_t l2_evict_last()
 {
-    asm volatile("red.global.add.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+// *p += v in FP64 at L2, without waiting for it (the owner thread is the only writer).
+__device__ __forceinline__ void red_add_f64(double *p, double v, uint64_t pol)
+{
+    asm volatile("red.global.add.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(pol)
+                 : "memory");
+}
+
+__device__ __forceinline__ void st_f64_hint(double *p, double v, uint64_t pol)
+{
+    asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(pol)
+                 : "memory");
 }
 
 // ---------------------------------------------------------------------------------
@@ -120,26 +136,40 @@ void launch_tcg_pack_blocks(const double *src, long long nblk, int ld, int Nd, i
 // [kcore (2)][8][8]: far field W [box][r][pd] (FP64), near field u gathered per leaf.
 // Rows r >= nr and columns s >= Kd are zero.
 // ---------------------------------------------------------------------------------
-__global__ void tcg_pack_x_kernel(const double *__restrict__ W, long long w_box_stride, int Kd,
-                                  int nbox, int nr, int Rp, int nch, int is_near, int d, int n,
-                                  int leaf, int L, const double *__restrict__ u, long long ldu,
-                                  uint16_t *__restrict__ dst)
+// Three-way BF16 split of x from one rounding to FP32: x ~ h = a1 + a2 + a3 exactly,
+// |x - h| <= 2^-24 |x|; the splits themselves are exact FP32 subtractions.
+__device__ __forceinline__ void bf16_split3_f32(double x, uint16_t &s1, uint16_t &s2, uint16_t &s3)
+{
+    const float h = __double2float_rn(x);
+    const __nv_bfloat16 a1 = __float2bfloat16_rn(h);
+    const float r1 = __fsub_rn(h, __bfloat162float(a1));
+    const __nv_bfloat16 a2 = __float2bfloat16_rn(r1);
+    const float r2 = __fsub_rn(r1, __bfloat162float(a2));
+    s1 = __bfloat16_as_ushort(a1);
+    s2 = __bfloat16_as_ushort(a2);
+    s3 = __bfloat16_as_ushort(__float2bfloat16_rn(r2));
+}
+
+// One thread per element of the packed tile layout of one box (grid.y = box): reads its
+// source value once (W [box][r][Kd] for the far field, u gathered from natural order for
+// the near field), writes its three split terms at the same position of the three split
+// planes.  Consecutive threads cover 8 columns x 4 rows of a core matrix pair, so the
+// reads come in 64-byte runs and each split's writes are contiguous.
+__global__ void __launch_bounds__(256) tcg_pack_x_kernel(
+    const double *__restrict__ W, long long w_box_stride, int Kd, int nbox, int nr, int Rp,
+    int nch, int is_near, int d, int n, int leaf, int L, const double *__restrict__ u,
+    long long ldu, uint16_t *__restrict__ dst)
 {
     const int NGa = Rp / 8;
-    const long long per_split = (long long)nch * NGa * 128;
-    const long long per_box = kSplits * per_split;
-    const long long total = per_box * nbox;
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const long long box = idx / per_box;
-        long long rem = idx % per_box;
-        const int split = (int)(rem / per_split);
-        rem %= per_split;
-        const int ch = (int)(rem / (NGa * 128));
-        rem %= NGa * 128;
-        const int g = (int)(rem / 128), o = (int)(rem % 128);
-        const int c = o / 64, row = (o % 64) / 8, e = o % 8;
-        const int r = g * 8 + row, s = ch * 16 + c * 8 + e;
+    const int per_split = nch * NGa * 128;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= per_split) return;
+    const int ch = idx / (NGa * 128);
+    const int rem = idx - ch * (NGa * 128);
+    const int g = rem >> 7, o = rem & 127;
+    const int c = o >> 6, row = (o >> 3) & 7, e = o & 7;
+    const int r = g * 8 + row, s = ch * 16 + c * 8 + e;
+    for (long long box = blockIdx.y; box < nbox; box += gridDim.y) {
         double x = 0.0;
         if (r < nr && s < Kd) {
             if (is_near) {
@@ -157,7 +187,12 @@ __global__ void tcg_pack_x_kernel(const double *__restrict__ W, long long w_box_
                 x = W[box * w_box_stride + (long long)r * Kd + s];
             }
         }
-        dst[idx] = bf16_split(x, split);
+        uint16_t s1, s2, s3;
+        bf16_split3_f32(x, s1, s2, s3);
+        uint16_t *out = dst + box * (long long)kSplits * per_split + idx;
+        out[0] = s1;
+        out[per_split] = s2;
+        out[2 * per_split] = s3;
     }
 }
 
@@ -165,8 +200,10 @@ void launch_tcg_pack_x(const double *W, long long w_box_stride, int Kd, int nbox
                        int nch, int is_near, int d, int n, int leaf, int L, const double *u,
                        long long ldu, uint16_t *dst, cudaStream_t s)
 {
-    tcg_pack_x_kernel<<<152 * 8, 256, 0, s>>>(W, w_box_stride, Kd, nbox, nr, Rp, nch, is_near, d,
-                                              n, leaf, L, u, ldu, dst);
+    const int per_split = nch * (Rp / 8) * 128;
+    dim3 grid((per_split + 255) / 256, nbox < 65535 ? nbox : 65535);
+    tcg_pack_x_kernel<<<grid, 256, 0, s>>>(W, w_box_stride, Kd, nbox, nr, Rp, nch, is_near, d, n,
+                                           leaf, L, u, ldu, dst);
 }
 
 // ---------------------------------------------------------------------------------
@@ -486,14 +523,15 @@ __global__ void __launch_bounds__(kGThreads, 1)
                         const int col0 = ps * Nw + my_c0;
                         const int lim = min(my_cols, A.Nd - col0);
                         o += col0;
+                        const uint64_t pol = l2_evict_last();
                         if (g0 > 0) {
 #pragma unroll
                             for (int i = 0; i < kMaxDrainChunks * 8; ++i)
-                                if (i < lim) red_add_f64(o + i, widen_f32(acc[i]));
+                                if (i < lim) red_add_f64(o + i, widen_f32(acc[i]), pol);
                         } else {
 #pragma unroll
                             for (int i = 0; i < kMaxDrainChunks * 8; ++i)
-                                if (i < lim) o[i] = widen_f32(acc[i]);
+                                if (i < lim) st_f64_hint(o + i, widen_f32(acc[i]), pol);
                         }
                     }
                 }
