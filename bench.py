@@ -72,11 +72,11 @@ def parse():
                          "each of them")
     ap.add_argument("--autotune-ms", type=float, default=2000.0,
                     help="htlr_autotune budget before timing (0: keep the default shapes)")
-    ap.add_argument("--serve-requests", type=int, default=120,
+    ap.add_argument("--serve-requests", type=int, default=32,
                     help="requests of the Poisson serving stream (0: skip serving)")
     ap.add_argument("--serve-rate", type=float, default=200.0)
-    ap.add_argument("--serve-max-n2", type=int, default=512)
-    ap.add_argument("--serve-max-n3", type=int, default=64)
+    ap.add_argument("--serve-max-n2", type=int, default=1024)
+    ap.add_argument("--serve-max-n3", type=int, default=128)
     ap.add_argument("--workloads", default="c2_fp64,c3,c4",
                     help="comma list of extra workloads measured after the headline and "
                          "reported under 'workloads' (empty: none)")
@@ -599,13 +599,18 @@ def time_serving(args):
     out = {"workload": f"{len(ops)} operators (d=2 n<={args.serve_max_n2} log; d=3 "
                        f"n<={args.serve_max_n3} 1/r, exp(-r); r in 5..7; SHARED), "
                        f"{args.serve_requests} requests, Poisson {args.serve_rate:g}/s, "
-                       "f ~ N(0,1), GMRES(30) to 1e-10"}
+                       "f ~ N(0,1), GMRES(30) to 1e-10",
+           "latency": "p50/p99: submission to completion (includes queueing behind earlier "
+                      "requests); service_*: admission to completion; queue_*: submission to "
+                      "admission"}
     for name, kw in arms.items():
         with htlr.Server(**kw) as S:
             ids = [S.add_operator(o.ktype, o.d, o.n, o.leaf, o.r, o.eta, a=o.a(), storage=2)
                    for o in ops]
-            for k, o in enumerate(ops):                 # warm: construct every operator
-                S.wait(S.submit(ids[k], serving.rhs(o, 1)))
+            # warm: construct every operator (a zero right-hand side finishes after the
+            # first residual, one matvec)
+            for k, o in enumerate(ops):
+                S.wait(S.submit(ids[k], np.zeros(o.N)))
             res = serving.replay(S, ops, stream, op_ids=ids)
             st = S.stats()
         res["batched_matvecs"] = st["batched_matvecs"]

@@ -232,8 +232,9 @@ int htlr_matvec_timed(const htlr_handle *H, const double *u, double *f, int nrhs
  *   - operators whose scratch would exceed 64 MiB are rejected with HTLR_ENOMEM and a
  *     message giving the size needed (e.g. c2, d=3 n=32, needs about 51 MB; the
  *     n=128 operators do not fit: use htlr_matvec);
- *   - the first call on a device looks up the array's device address there (with that
- *     device current); make that first call before any CUDA stream capture;
+ *   - every call looks up the array's device address on the current device (an
+ *     allocation-free query); the first call on a device may load the library's device
+ *     code there, so make it before any CUDA stream capture;
  *   - every call on a device shares the same array: calls whose GPU work overlaps (other
  *     streams, other threads) race; nothing needs clearing between calls;
  *   - every GPU that loads the library holds the 64 MiB until the process exits.
@@ -447,6 +448,11 @@ const char *htlr_last_error(void);
  * products included) one htlr_matvec of nrhs right-hand sides executes on H; 0 when H
  * has no BF16X6 block list.  Host-side count, no device work. */
 double htlr_tensor_flops(const htlr_handle *H, int nrhs);
+
+/* Device allocations (cudaMalloc) the library has made in this process so far: every
+ * entry point allocates through one counted helper, so a caller can check that a call
+ * (htlr_matvec_noalloc, for instance) allocated nothing. */
+long long htlr_device_allocations(void);
 
 /* Number of kernel launches the last htlr_matvec on H enqueued. */
 int htlr_last_launch_count(const htlr_handle *H);

@@ -11,6 +11,8 @@
 //           f_tau = sum_sigma A_{tau sigma} u_sigma     every inadmissible leaf
 //   out     f_tau += sum_levels H_anc x_1 U_1 ... x_d U_d  restricted to the leaf's rows
 // The stream step reads every core and dense block once; it is the hot loop.
+#include <algorithm>
+
 #include "htlr_internal.h"
 
 namespace htlr {
@@ -113,7 +115,8 @@ __device__ __forceinline__ BoxDims box_dims(const LevelGeom &g, int d, int box)
 template <class AR>
 __global__ void __launch_bounds__(128) up_kernel(int d, int n, LevelGeom g,
                                                  const double *__restrict__ u, long long ldu,
-                                                 int nrc, double *__restrict__ W, int slab)
+                                                 int nrc, double *__restrict__ W, int slab,
+                                                 int urows, int vsm)
 {
     using T = typename AR::T;
     extern __shared__ __align__(16) unsigned char up_sm[];
@@ -122,42 +125,51 @@ __global__ void __launch_bounds__(128) up_kernel(int d, int n, LevelGeom g,
     const int pe = g.pe, mc = g.maxcnt;
     const BoxDims b = box_dims(g, d, box);
     const double *ur = u + ldu * r;
+    const int n3 = (d == 3) ? mc : 1;
     T *Vs = sm;                           // d factors, mc x pe each (leading dim cnt_k)
-    T *Y1 = Vs + 3 * mc * pe;             // pe x c2 x slab
+    T *Y1 = Vs + (vsm ? 3 * mc * pe : 0); // pe x c2 x slab
     T *Y2 = Y1 + pe * mc * slab;          // pe x pe x c3
-    T *Us = Y2 + pe * pe * mc;            // the slab of u_sigma, c1 x c2 x slab, converted once
-    for (int k = 0; k < d; ++k)
-        for (int i = threadIdx.x; i < b.cnt[k] * pe; i += blockDim.x)
-            Vs[k * mc * pe + i] = AR::from(b.V[k][i]);
-    __syncthreads();
+    T *Us = Y2 + pe * pe * n3;            // rows of u_sigma (c1 values each), converted once
+    // the factors in shared memory when they fit (vsm), else read (and converted) in place
+    if (vsm) {
+        for (int k = 0; k < d; ++k)
+            for (int i = threadIdx.x; i < b.cnt[k] * pe; i += blockDim.x)
+                Vs[k * mc * pe + i] = AR::from(b.V[k][i]);
+        __syncthreads();
+    }
     const int c1 = b.cnt[0], c2 = b.cnt[1], c3 = (d == 3) ? b.cnt[2] : 1;
-    const T *V1 = Vs, *V2 = Vs + mc * pe, *V3 = Vs + 2 * mc * pe;
+    auto vf = [&](int k, int i) -> T { return vsm ? Vs[k * mc * pe + i] : AR::from(b.V[k][i]); };
     const long long base = (long long)b.first[0] + (long long)n * b.first[1] +
                            (d == 3 ? (long long)n * n * b.first[2] : 0);
     for (int i3g = 0; i3g < c3; i3g += slab) {
         const int ns = min(slab, c3 - i3g);
-        for (int idx = threadIdx.x; idx < c1 * c2 * ns; idx += blockDim.x) {
-            const int i1 = idx % c1, rest = idx / c1;
-            const int i2 = rest % c2, j3 = rest / c2;
-            Us[idx] = AR::from(ur[base + i1 + (long long)n * i2 + (long long)n * n * (i3g + j3)]);
+        // mode 1: Y1[mu1 + pe (i2 + c2 j3)] = sum_i1 V1[i1, mu1] u[i1, i2, i3], over the
+        // rows (i2, j3) of the slab in chunks of `urows` rows staged in shared memory
+        const int nrow = c2 * ns;
+        for (int r0 = 0; r0 < nrow; r0 += urows) {
+            const int nr = min(urows, nrow - r0);
+            for (int idx = threadIdx.x; idx < c1 * nr; idx += blockDim.x) {
+                const int i1 = idx % c1, row = r0 + idx / c1;
+                const int i2 = row % c2, j3 = row / c2;
+                Us[idx] = AR::from(ur[base + i1 + (long long)n * i2 + (long long)n * n * (i3g + j3)]);
+            }
+            __syncthreads();
+            for (int idx = threadIdx.x; idx < pe * nr; idx += blockDim.x) {
+                const int mu1 = idx % pe, row = idx / pe;
+                const T *ru = Us + c1 * row;
+                T acc = AR::zero();
+                for (int i1 = 0; i1 < c1; ++i1) acc = AR::mac(vf(0, i1 + c1 * mu1), ru[i1], acc);
+                Y1[mu1 + pe * (r0 + row)] = acc;
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        // mode 1: Y1[mu1 + pe (i2 + c2 j3)] = sum_i1 V1[i1, mu1] u[i1, i2, i3]
-        for (int idx = threadIdx.x; idx < pe * c2 * ns; idx += blockDim.x) {
-            int mu1 = idx % pe, rest = idx / pe;
-            const T *row = Us + c1 * rest;
-            T acc = AR::zero();
-            for (int i1 = 0; i1 < c1; ++i1) acc = AR::mac(V1[i1 + c1 * mu1], row[i1], acc);
-            Y1[idx] = acc;
-        }
-        __syncthreads();
         // mode 2: Y2[mu1 + pe (mu2 + pe i3)] = sum_i2 V2[i2, mu2] Y1[mu1 + pe (i2 + c2 j3)]
         for (int idx = threadIdx.x; idx < pe * pe * ns; idx += blockDim.x) {
             int mu1 = idx % pe, rest = idx / pe;
             int mu2 = rest % pe, j3 = rest / pe;
             T acc = AR::zero();
             for (int i2 = 0; i2 < c2; ++i2)
-                acc = AR::mac(V2[i2 + c2 * mu2], Y1[mu1 + pe * (i2 + c2 * j3)], acc);
+                acc = AR::mac(vf(1, i2 + c2 * mu2), Y1[mu1 + pe * (i2 + c2 * j3)], acc);
             Y2[mu1 + pe * (mu2 + pe * (i3g + j3))] = acc;
         }
         __syncthreads();
@@ -172,7 +184,7 @@ __global__ void __launch_bounds__(128) up_kernel(int d, int n, LevelGeom g,
     for (int idx = threadIdx.x; idx < pd; idx += blockDim.x) {
         int m12 = idx % (pe * pe), mu3 = idx / (pe * pe);
         T acc = AR::zero();
-        for (int i3 = 0; i3 < c3; ++i3) acc = AR::mac(V3[i3 + c3 * mu3], Y2[m12 + pe * pe * i3], acc);
+        for (int i3 = 0; i3 < c3; ++i3) acc = AR::mac(vf(2, i3 + c3 * mu3), Y2[m12 + pe * pe * i3], acc);
         Wout[idx] = AR::to(acc);
     }
 }
@@ -183,23 +195,25 @@ void launch_up(int d, int n, const LevelGeom &g, const double *u, int nrhs_here,
     const int nbox = 1 << (d * g.level);
     const int mc = g.maxcnt, pe = g.pe;
     const int n3 = (d == 3) ? mc : 1;
-    // slab of the last dimension so that the staged u and the mode-1 buffer stay within
-    // 64 KB
+    // slab of the last dimension so that the mode-1 buffer stays within 64 KB, and rows of
+    // u staged 4096 values at a time
     int slab = n3;
-    while (slab > 1 && (long long)(pe + mc) * mc * slab > 8192) slab = (slab + 1) / 2;
-    size_t smem = sizeof(double) * ((size_t)3 * mc * pe + (size_t)pe * mc * slab +
-                                    (size_t)pe * pe * mc + (size_t)mc * mc * slab);
+    while (slab > 1 && (long long)pe * mc * slab > 8192) slab = (slab + 1) / 2;
+    const int urows = std::max(1, 4096 / mc);
+    const int vsm = 3 * mc * pe <= 8192 ? 1 : 0;   // factors staged when within 64 KB
+    size_t smem = sizeof(double) * ((vsm ? (size_t)3 * mc * pe : 0) + (size_t)pe * mc * slab +
+                                    (size_t)pe * pe * n3 + (size_t)mc * urows);
     dim3 grid(nbox, nrhs_here);
     if (df64) {
         if (smem > 48 * 1024)
             cudaFuncSetAttribute(up_kernel<ArithDF64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
-        up_kernel<ArithDF64><<<grid, 128, smem, s>>>(d, n, g, u, ldu, nrc, d_W, slab);
+        up_kernel<ArithDF64><<<grid, 128, smem, s>>>(d, n, g, u, ldu, nrc, d_W, slab, urows, vsm);
     } else {
         if (smem > 48 * 1024)
             cudaFuncSetAttribute(up_kernel<ArithFP64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
-        up_kernel<ArithFP64><<<grid, 128, smem, s>>>(d, n, g, u, ldu, nrc, d_W, slab);
+        up_kernel<ArithFP64><<<grid, 128, smem, s>>>(d, n, g, u, ldu, nrc, d_W, slab, urows, vsm);
     }
 }
 

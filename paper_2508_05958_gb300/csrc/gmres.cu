@@ -306,13 +306,13 @@ extern "C" int htlr_gmres(const htlr_handle *H, const htlr_handle *H_inner, cons
     W.m = O.restart;
     const size_t vec = (size_t)N * nrhs;
     cudaError_t e;
-    if ((e = cudaMalloc(&W.V, sizeof(double) * vec * (W.m + 1))) != cudaSuccess ||
-        (e = cudaMalloc(&W.w, sizeof(double) * vec)) != cudaSuccess ||
-        (e = cudaMalloc(&W.r, sizeof(double) * vec)) != cudaSuccess ||
-        (e = cudaMalloc(&W.part, sizeof(double) * kDotBlocks * nrhs * (W.m + 1))) != cudaSuccess ||
-        (e = cudaMalloc(&W.c, sizeof(double) * nrhs * (W.m + 1))) != cudaSuccess ||
-        (e = cudaMalloc(&W.c2, sizeof(double) * nrhs * (W.m + 1))) != cudaSuccess ||
-        (e = cudaMalloc(&W.nn, sizeof(double) * nrhs)) != cudaSuccess)
+    if ((e = device_malloc((void **)&W.V, sizeof(double) * vec * (W.m + 1))) != cudaSuccess ||
+        (e = device_malloc((void **)&W.w, sizeof(double) * vec)) != cudaSuccess ||
+        (e = device_malloc((void **)&W.r, sizeof(double) * vec)) != cudaSuccess ||
+        (e = device_malloc((void **)&W.part, sizeof(double) * kDotBlocks * nrhs * (W.m + 1))) != cudaSuccess ||
+        (e = device_malloc((void **)&W.c, sizeof(double) * nrhs * (W.m + 1))) != cudaSuccess ||
+        (e = device_malloc((void **)&W.c2, sizeof(double) * nrhs * (W.m + 1))) != cudaSuccess ||
+        (e = device_malloc((void **)&W.nn, sizeof(double) * nrhs)) != cudaSuccess)
         return cuda_fail(e, "htlr_gmres workspace");
     int iters = 0, matvecs = 0, refinements = 0, rc;
     std::vector<double> rel;
@@ -321,10 +321,10 @@ extern "C" int htlr_gmres(const htlr_handle *H, const htlr_handle *H_inner, cons
         if (rc) return rc;
     } else {
         // iterative refinement: residual with H (accurate), corrections with H_inner
-        if ((e = cudaMalloc(&W.e, sizeof(double) * vec)) != cudaSuccess)
+        if ((e = device_malloc((void **)&W.e, sizeof(double) * vec)) != cudaSuccess)
             return cuda_fail(e, "htlr_gmres workspace");
         double *rr = nullptr;
-        if ((e = cudaMalloc(&rr, sizeof(double) * vec)) != cudaSuccess)
+        if ((e = device_malloc((void **)&rr, sizeof(double) * vec)) != cudaSuccess)
             return cuda_fail(e, "htlr_gmres workspace");
         std::vector<double> fn, rn;
         rc = dots(W, H->stream, f, f, 1, W.c, &fn);

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <atomic>
 #include <mutex>
 #include <new>
 #include <set>
@@ -36,6 +37,14 @@ int cuda_fail(cudaError_t e, const char *what)
         if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
     } while (0)
 
+static std::atomic<long long> g_device_allocs{0};
+
+cudaError_t device_malloc(void **p, size_t bytes)
+{
+    g_device_allocs.fetch_add(1, std::memory_order_relaxed);
+    return cudaMalloc(p, bytes);
+}
+
 static int fail(int code, const std::string &msg)
 {
     set_error(msg);
@@ -48,7 +57,7 @@ static int dalloc(htlr_handle *H, T **p, size_t count)
     *p = nullptr;
     if (count == 0) count = 1;
     void *q = nullptr;
-    cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+    cudaError_t e = device_malloc(&q, count * sizeof(T));
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
     H->allocs.push_back(q);
     *p = static_cast<T *>(q);
@@ -82,7 +91,7 @@ struct Temps {
         *out = nullptr;
         if (count == 0) count = 1;
         void *q = nullptr;
-        cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+        cudaError_t e = device_malloc(&q, count * sizeof(T));
         if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (temporary)");
         p.push_back(q);
         *out = static_cast<T *>(q);
@@ -733,7 +742,7 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
             const size_t nel = (size_t)Lv.ncores * Lv.ld * Lv.pd;
             double *dcore = nullptr;
             if (H->far_prec == kPrecFP32 || H->far_prec == kPrecBF16X6) {
-                HTLR_CK(cudaMalloc(&dcore, nel * sizeof(double)));
+                HTLR_CK(device_malloc((void **)&dcore, nel * sizeof(double)));
             } else if (dalloc(H, &dcore, nel)) {
                 return HTLR_ECUDA;
             }
@@ -865,7 +874,7 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
         const size_t nel = (size_t)H->nnear_unique * H->near_ld * rows_leaf;
         double *dnear = nullptr;
         if (H->near_prec == kPrecFP32 || H->near_prec == kPrecBF16X6) {
-            HTLR_CK(cudaMalloc(&dnear, nel * sizeof(double)));
+            HTLR_CK(device_malloc((void **)&dnear, nel * sizeof(double)));
         } else if (dalloc(H, &dnear, nel)) {
             return HTLR_ECUDA;
         }
@@ -1613,8 +1622,8 @@ int htlr_matvec_host(htlr_handle *H, const double *u_host, double *f_host, int n
         if (H->d_stage_f) cudaFree(H->d_stage_f);
         H->d_stage_u = H->d_stage_f = nullptr;
         H->stage_cap = 0;
-        HTLR_CK(cudaMalloc(&H->d_stage_u, need * sizeof(double)));
-        HTLR_CK(cudaMalloc(&H->d_stage_f, need * sizeof(double)));
+        HTLR_CK(device_malloc((void **)&H->d_stage_u, need * sizeof(double)));
+        HTLR_CK(device_malloc((void **)&H->d_stage_f, need * sizeof(double)));
         H->stage_cap = need;
     }
     HTLR_CK(cudaMemcpyAsync(H->d_stage_u, u_host, need * sizeof(double), cudaMemcpyHostToDevice,
@@ -1672,6 +1681,8 @@ int htlr_set_wait_limit(htlr_handle *H, long long cycles)
     ++H->generation;   // captured plans hold the old limit in their launch arguments
     return HTLR_OK;
 }
+
+long long htlr_device_allocations(void) { return g_device_allocs.load(std::memory_order_relaxed); }
 
 double htlr_tensor_flops(const htlr_handle *H, int nrhs)
 {

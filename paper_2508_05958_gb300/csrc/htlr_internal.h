@@ -201,6 +201,10 @@ namespace htlr {
 // Error reporting (thread-local message).
 void set_error(const std::string &msg);
 int cuda_fail(cudaError_t e, const char *what);
+// Every device allocation the library makes goes through device_malloc, which counts
+// them (htlr_device_allocations) so that a caller can check that an entry point
+// allocated nothing.
+cudaError_t device_malloc(void **p, size_t bytes);
 // After the handle's stream has drained: read and clear its device error word
 // (HTLR_ETIMEOUT for a bounded wait that ran out, HTLR_EDEVICE for other checks).
 int check_device_error(const htlr_handle *H, const char *what);

@@ -15,7 +15,6 @@
 // ordering) race and produce wrong results.  Every byte a call reads is written earlier
 // in the same call, so nothing has to be cleared between calls.
 #include <cstdio>
-#include <mutex>
 #include <vector>
 
 #include "htlr_internal.h"
@@ -28,27 +27,16 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratch
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mu;
-unsigned char *g_scratch_addr[kMaxDevices] = {nullptr};
-
-// Device address of the static scratch on the current device, looked up once per device
-// with that device current.  The host-side symbol g_noalloc_scratch is only a stand-in
-// and must never be passed to a kernel.
-int scratch_address(int device, unsigned char **out)
+// Device address of the static scratch on the current device.  It is looked up on every
+// call (cudaGetSymbolAddress allocates nothing), so it stays right after the context has
+// been reset or recreated.  The host-side symbol g_noalloc_scratch is only a stand-in and
+// must never be passed to a kernel.
+int scratch_address(unsigned char **out)
 {
-    if (device < 0 || device >= kMaxDevices) {
-        set_error("htlr_matvec_noalloc: device index out of range");
-        return HTLR_EINVAL;
-    }
-    std::lock_guard<std::mutex> g(g_setup_mu);
-    if (!g_scratch_addr[device]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
-        g_scratch_addr[device] = static_cast<unsigned char *>(p);
-    }
-    *out = g_scratch_addr[device];
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+    *out = static_cast<unsigned char *>(p);
     return HTLR_OK;
 }
 
@@ -104,7 +92,7 @@ int matvec_noalloc(const htlr_handle *H, const double *u, double *f, int nrhs)
         return HTLR_ENOMEM;
     }
     unsigned char *base = nullptr;
-    int rc = scratch_address(H->device, &base);
+    int rc = scratch_address(&base);
     if (rc) return rc;
 
     // task kinds pointing at the scratch W tensors (copied from host memory)

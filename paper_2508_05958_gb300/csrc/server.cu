@@ -336,13 +336,13 @@ int htlr_server::make_group(Operator &op, Group &g, int prec_far, int prec_near,
         if ((rc = htlr_autotune(g.H, B, o.autotune_ms, &tr))) return rc;
     }
     const int maxcnt = m + 1;
-    if ((e = cudaMalloc(&g.Ub, sizeof(double) * op.N * B)) != cudaSuccess ||
-        (e = cudaMalloc(&g.Fb, sizeof(double) * op.N * B)) != cudaSuccess ||
-        (e = cudaMalloc(&g.d_part, sizeof(double) * (size_t)B * kBlk * maxcnt)) != cudaSuccess ||
-        (e = cudaMalloc(&g.d_out, sizeof(double) * (size_t)B * S)) != cudaSuccess ||
-        (e = cudaMalloc(&g.d_coef, sizeof(double) * (size_t)B * S)) != cudaSuccess ||
-        (e = cudaMalloc(&g.d_dot, sizeof(DotDesc) * (size_t)B * 3)) != cudaSuccess ||
-        (e = cudaMalloc(&g.d_vec, sizeof(VecDesc) * (size_t)B * 3)) != cudaSuccess)
+    if ((e = device_malloc((void **)&g.Ub, sizeof(double) * op.N * B)) != cudaSuccess ||
+        (e = device_malloc((void **)&g.Fb, sizeof(double) * op.N * B)) != cudaSuccess ||
+        (e = device_malloc((void **)&g.d_part, sizeof(double) * (size_t)B * kBlk * maxcnt)) != cudaSuccess ||
+        (e = device_malloc((void **)&g.d_out, sizeof(double) * (size_t)B * S)) != cudaSuccess ||
+        (e = device_malloc((void **)&g.d_coef, sizeof(double) * (size_t)B * S)) != cudaSuccess ||
+        (e = device_malloc((void **)&g.d_dot, sizeof(DotDesc) * (size_t)B * 3)) != cudaSuccess ||
+        (e = device_malloc((void **)&g.d_vec, sizeof(VecDesc) * (size_t)B * 3)) != cudaSuccess)
         return cuda_fail(e, "server: batch buffers");
     if ((rc = pinned(&g.h_dot, (size_t)B * 3)) || (rc = pinned(&g.h_vec, (size_t)B * 3)) ||
         (rc = pinned(&g.h_out, (size_t)B * S)) || (rc = pinned(&g.h_coef, (size_t)B * S)))
@@ -432,7 +432,7 @@ void htlr_server::admit()
             }
             continue;
         }
-        cudaError_t e = cudaMalloc(&q->ws, need);
+        cudaError_t e = device_malloc((void **)&q->ws, need);
         if (e != cudaSuccess) {
             it = pending.erase(it);
             finish(q, cuda_fail(e, "server: request workspace"));

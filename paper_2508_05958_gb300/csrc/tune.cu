@@ -92,8 +92,8 @@ extern "C" int htlr_autotune(htlr_handle *H, int nrhs, double budget_ms, htlr_tu
     long long N = 1;
     for (int k = 0; k < H->d; ++k) N *= H->n;
     double *u = nullptr, *f = nullptr;
-    cudaError_t e = cudaMalloc(&u, sizeof(double) * N * nrhs);
-    if (e == cudaSuccess) e = cudaMalloc(&f, sizeof(double) * N * nrhs);
+    cudaError_t e = device_malloc((void **)&u, sizeof(double) * N * nrhs);
+    if (e == cudaSuccess) e = device_malloc((void **)&f, sizeof(double) * N * nrhs);
     if (e != cudaSuccess) {
         if (u) cudaFree(u);
         return cuda_fail(e, "htlr_autotune: scratch vectors");

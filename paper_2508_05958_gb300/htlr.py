@@ -29,7 +29,8 @@ SYMBOLS = ("htlr_construct", "htlr_construct_ex", "htlr_matvec", "htlr_matvec_ti
            "htlr_plan_launches", "htlr_plan_free", "htlr_autotune", "htlr_autotune_clear_cache",
            "htlr_server_create", "htlr_server_add_operator", "htlr_server_submit",
            "htlr_server_poll", "htlr_server_wait", "htlr_server_get_stats",
-           "htlr_server_destroy", "htlr_tensor_flops", "htlr_set_wait_limit")
+           "htlr_server_destroy", "htlr_tensor_flops", "htlr_set_wait_limit",
+           "htlr_device_allocations")
 
 
 class HTLRError(RuntimeError):
@@ -173,6 +174,8 @@ def load(build_if_missing: bool = True):
         L.htlr_set_stream.restype = ctypes.c_int
         L.htlr_sync.argtypes = [vp]
         L.htlr_sync.restype = ctypes.c_int
+        L.htlr_device_allocations.argtypes = []
+        L.htlr_device_allocations.restype = ctypes.c_longlong
         L.htlr_set_wait_limit.argtypes = [vp, ctypes.c_longlong]
         L.htlr_set_wait_limit.restype = ctypes.c_int
         L.htlr_last_error.argtypes = []

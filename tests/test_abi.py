@@ -11,7 +11,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def declared_symbols():
     src = open(os.path.join(ROOT, "include", "htlr.h")).read()
-    pat = r"^(?:const\s+char\s*\*|int|void|double)\s*\*?\s*(htlr_[a-z_]+)\s*\("
+    pat = r"^(?:const\s+char\s*\*|long\s+long|int|void|double)\s*\*?\s*(htlr_[a-z_]+)\s*\("
     return sorted(set(re.findall(pat, src, flags=re.M)))
 
 

@@ -460,3 +460,22 @@ def test_zero_and_constant_inputs():
         assert torch.allclose(f, torch.full_like(f, expect), rtol=0, atol=1e-12 * abs(expect) + 1e-14)
     finally:
         htlr.htlr_free(H)
+
+
+@pytest.mark.parametrize("case", [dict(n=512, leaf=8, p=6, eta=math.sqrt(2.0), k=0, sig=0.0),
+                                  dict(n=1024, leaf=8, p=7, eta=math.sqrt(2.0), k=0, sig=0.0),
+                                  dict(n=2048, leaf=16, p=8, eta=0.0, k=3, sig=math.sqrt(2.0))])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_large_2d_boxes_match_oracle_rows(oracle, case, prec):
+    """2D operators whose upper levels hold large boxes (128^2 to 1024^2 points): the
+    upward and downward contractions stage their data in bounded pieces of shared
+    memory.  FP64 and df64 against the oracle's row-sampled HTLR."""
+    from paper_2508_05958_gb300.workloads import Workload
+    w = Workload("big2d", d=2, n=case["n"], ktype=case["k"], leaf=case["leaf"], p=case["p"],
+                 eta=case["eta"], kparam=case["sig"], a_kind="one", seed=51)
+    u = w.u(nrhs=2)
+    rows = w.sample_rows(12, seed=52)
+    f, info = gpu_matvec(w, u, storage=2, far_precision=prec, near_precision=prec)
+    ref = oracle.htlr_rows(w.d, w.n, w.ktype, w.leaf, w.p, w.eta, u, rows, param=w.kparam,
+                           a=w.a())
+    assert rel(f[rows], ref) < TOL
