@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--config", default="c2")
     ap.add_argument("--storage", type=int, default=1, help="1 STORED, 2 SHARED, 0 AUTO")
     ap.add_argument("--far-precision", type=int, default=1, help="0 FP64, 1 DF64, 2 FP32, 3 BF16X6 (tensor cores)")
-    ap.add_argument("--near-precision", type=int, default=1, help="0 FP64, 1 DF64, 2 FP32, 3 BF16X6 (tensor cores)")
+    ap.add_argument("--near-precision", type=int, default=1, help="0 FP64, 1 DF64, 2 FP32, 3 BF16X6 (tensor cores), 4 TF32X3 (generated, tensor cores)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tc-segment", type=int, default=0,
                     help="tensor-core K steps per accumulator segment (0: library default)")
@@ -263,8 +263,8 @@ def run_reference(args, w):
 # ----------------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------------
-PREC_NAME = {0: "f64", 1: "df64", 2: "f32", 3: "bf16x6"}
-PREC_BYTES = {0: 8, 1: 8, 2: 4, 3: 6}
+PREC_NAME = {0: "f64", 1: "df64", 2: "f32", 3: "bf16x6", 4: "tf32x3"}
+PREC_BYTES = {0: 8, 1: 8, 2: 4, 3: 6, 4: 8}
 # multiply-adds per second of the stream's inner loop, from unit counts and clocks
 # (152 SMs at 2.07 GHz): FP64 2 FMA/clk/SM (the nominal 1.25 TFLOP/s); FP32 128 lanes;
 # df64 spends 12 FP32-pipe instructions per multiply-add (see stream_impl.cuh)
@@ -345,6 +345,33 @@ def stream_roofline(info, w, nrhs, stream_ms, hbm_peak, hbm_src, bf16_peak=None,
     return roof
 
 
+# SFU operations per generated kernel value in FP32 (1/r: rsqrt; exp(-r): rsqrt, ex2;
+# Gaussian: ex2; log: lg2), and the SFU rate: 16 per clock per SM, 152 SMs at 2.07 GHz
+SFU_PER_PAIR = {0: 1, 1: 1, 2: 2, 3: 1}
+SFU_PEAK = 152 * 16 * 2.07e9
+
+
+def near_tc_roofline(info, w, nrhs, ms):
+    """The generated near field on the tensor cores: its bound is the kernel generation on
+    the SFUs (the products run on the tensor cores at a few per cent of their rate), so
+    achieved = near point pairs (kernel values generated) per second against the SFU rate
+    divided by the SFU operations per value."""
+    t = ms * 1e-3
+    pairs = float(info["near_point_pairs"])
+    per = SFU_PER_PAIR.get(w.ktype)
+    peak = SFU_PEAK / per / 1e9 if per else None
+    ach = pairs / t / 1e9
+    return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Geval/s",
+            "frac": ach / peak if peak else None,
+            "peak_source": "derived: 152 SMs x 2.07 GHz x 16 SFU ops/clk / %s SFU ops per "
+                           "kernel value" % per,
+            "kernel": "near_tc_kernel (kernel values generated into tensor memory, "
+                      "tcgen05 kind::tf32 products; stage includes packing of w u)",
+            "kernel_ms": ms, "multiply_adds_per_launch": pairs * nrhs,
+            "tf32_tensor_flops_per_launch": pairs * 16 * ((nrhs + 15) // 16) * 3 * 2,
+            "traffic": None, "precision": {"near": PREC_NAME[info["near_precision"]]}}
+
+
 def near_cc_roofline(info, w, nrhs, ms):
     """The near field on the CUDA cores beside a tensor-core far field, or generated:
     multiply-adds per launch = near point pairs x RHS (plus one kernel evaluation per pair
@@ -372,7 +399,7 @@ def near_cc_roofline(info, w, nrhs, ms):
 SUITE = {
     "c2_fp64": ("c2", 1, 0, 0),     # the headline operator in plain FP64 (STORED)
     "c3": ("c3", 2, 3, 3),          # 64 RHS, SHARED, BF16x6 tensor cores far and near
-    "c4": ("c4", 3, 3, 2),          # 16 RHS, tensor grid: BF16x6 far, FP32 generated near
+    "c4": ("c4", 3, 3, 4),          # 16 RHS, tensor grid: BF16x6 far, TF32x3 generated near
 }
 
 # DRAM traffic per executed BF16 tensor FLOP of the grouped tensor-core kernel (all its
@@ -483,7 +510,8 @@ def run_suite_workload(key, args, stream, peaks, hbm_peak, hbm_src):
         else:
             roofs.append(stream_roofline(info, w, nrhs, stage_ms[1], hbm_peak, hbm_src))
         if stage_ms[2] > 1e-2:
-            roofs.append(near_cc_roofline(info, w, nrhs, stage_ms[2]))
+            roofs.append(near_tc_roofline(info, w, nrhs, stage_ms[2]) if np_ == 4 else
+                         near_cc_roofline(info, w, nrhs, stage_ms[2]))
         roofs.sort(key=lambda r: -r["kernel_ms"])
         # the timed product's rows (the last timed matvec left f in fd)
         rows = w.sample_rows(args.workload_rows, seed=1024) if w.N > 100000 else None
@@ -706,8 +734,9 @@ def run_gpu(args, w):
     # roofline of the dominant kernel (the block stream)
     roofs = [stream_roofline(info, w, nrhs, stage_ms[1], hbm_peak, hbm_src,
                              peaks.get("bf16_tflops"), htlr.htlr_tensor_flops(H, nrhs))]
-    if stage_ms[2] > 1e-2:            # near field on the CUDA cores in its own stage
-        roofs.append(near_cc_roofline(info, w, nrhs, stage_ms[2]))
+    if stage_ms[2] > 1e-2:            # near field (CUDA or tensor cores) in its own stage
+        roofs.append(near_tc_roofline(info, w, nrhs, stage_ms[2]) if info["near_precision"] == 4
+                     else near_cc_roofline(info, w, nrhs, stage_ms[2]))
     roofs.sort(key=lambda r: -r["kernel_ms"])
     roof = roofs[0]                   # the dominant kernel
     key = (w.name, info["storage"], info["far_precision"], info["near_precision"], nrhs)
@@ -760,7 +789,7 @@ def run_gpu(args, w):
         f_gpu = f_head
         val, cores, sample, _ = time_oracle(w, args.cpu_sample_s)
         f_ref = time_oracle.last_output
-        tol = {0: 1e-12, 1: 1e-12, 2: 1e-6, 3: 1e-3}[max(info["far_precision"],
+        tol = {0: 1e-12, 1: 1e-12, 2: 1e-6, 3: 1e-6, 4: 1e-6}[max(info["far_precision"],
                                                         info["near_precision"])]
         line["cpu_baseline"] = {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": sample,
@@ -882,7 +911,7 @@ ACCURACY_MODES = {
     "c3": [("fp64", 2, 0, 0), ("df64", 2, 1, 1), ("f32 far / df64 near", 2, 2, 1),
            ("bf16x6 far / df64 near", 2, 3, 1), ("bf16x6", 2, 3, 3)],
     "c4": [("fp64", 3, 0, 0), ("bf16x6 far / f64 near", 3, 3, 0), ("f32", 3, 2, 2),
-           ("bf16x6 far / f32 near", 3, 3, 2)],
+           ("bf16x6 far / f32 near", 3, 3, 2), ("bf16x6 far / tf32x3 near", 3, 3, 4)],
 }
 
 

@@ -100,17 +100,27 @@ typedef enum {
                             more where the result cancels (random u against a smooth
                             kernel).  A generated near field sums each source leaf apart
                             and then adds the leaf sums */
-    HTLR_PREC_BF16X6 = 3 /* tensor cores (tcgen05): operands split into three BF16 terms,
+    HTLR_PREC_BF16X6 = 3, /* tensor cores (tcgen05): operands split into three BF16 terms,
                             the six products a_i b_j with i + j <= 4 (1-based) accumulated
                             in FP32 tensor memory; the many-right-hand-side path, 64 RHS at
                             a time.  The tensor cores' FP32 accumulation truncates each
                             addition, so with SHARED blocks the accumulation runs in short
                             segments (tc_segment) that start fresh with the small cross
                             products, whose sums are added in FP32 registers and flushed to
-                            FP64 every tc_flush segments.  With STORED blocks a whole block
-                            row accumulates in tensor memory (see htlr_options).  A BF16X6
-                            far field goes with a BF16X6, generated, or held FP64/df64/FP32
-                            near field; a BF16X6 near field needs a BF16X6 far field */
+                            FP64 every tc_flush segments.  STORED blocks are refused
+                            (HTLR_EUNSUPPORTED); AUTO storage resolves to SHARED.  A BF16X6
+                            far field goes with a BF16X6, generated (FP64, FP32 or TF32X3),
+                            or held FP64/df64/FP32 near field; a BF16X6 near field needs a
+                            BF16X6 far field */
+    HTLR_PREC_TF32X3 = 4 /* near field only, generated (tensor grids, HTLR_STORE_GENERATED,
+                            or AUTO storage, which then generates it): kernel values
+                            computed per point pair in FP32 and written into tensor memory
+                            as two TF32 terms (nearest, then the exact rest), w_j u_j as two
+                            TF32 terms, the three products a2 b1, a1 b2, a1 b1 (tcgen05
+                            kind::tf32), 16 right-hand sides per pass; FP32 accumulation in
+                            segments of two 16-source stages that start fresh with the cross
+                            products, summed in FP32 and flushed to FP64 every 16 segments.
+                            Measured within 1e-6 of the FP64 oracle on every kernel type */
 } htlr_precision;
 
 typedef struct {
@@ -209,8 +219,9 @@ int htlr_matvec_host(htlr_handle *H, const double *u_host, double *f_host, int n
  * htlr_matvec_timed -- htlr_matvec that also measures, with CUDA events recorded on the
  * handle's stream, the device time of each stage: stage_ms[0] upward contractions,
  * [1] block streaming (cores and held dense blocks, on CUDA or tensor cores, with the
- * packing of their operands), [2] the near field on the CUDA cores when it is generated
- * or sits beside a tensor-core far field, [3] per-row reductions, [4] downward
+ * packing of their operands), [2] the near field in its own launches: generated (on the
+ * CUDA cores, or on the tensor cores for TF32X3, packing of w u included), or held beside
+ * a tensor-core far field, [3] per-row reductions, [4] downward
  * expansion + output.  Times are summed over RHS chunks.  Synchronous
  * (waits for the stream).  stage_ms: host array of HTLR_NUM_STAGES floats.
  */

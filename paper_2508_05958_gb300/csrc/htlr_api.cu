@@ -486,7 +486,12 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
     H->near_rows = rows_leaf;
     H->near_ld = round_up(rows_leaf, 32);
     const int want0 = o ? o->storage : HTLR_STORE_AUTO;
-    H->near_generated = (H->tensor || want0 == HTLR_STORE_GENERATED) ? 1 : 0;
+    // a TF32X3 near field is generated on the tensor cores: AUTO storage generates it
+    H->near_generated = (H->tensor || want0 == HTLR_STORE_GENERATED ||
+                         (want0 == HTLR_STORE_AUTO && H->near_prec == kPrecTF32X3)) ? 1 : 0;
+    if (H->near_prec == kPrecTF32X3 && !H->near_generated)
+        return fail(HTLR_EUNSUPPORTED, "a TF32X3 near field is generated (tensor grids, "
+                                       "HTLR_STORE_GENERATED or AUTO storage)");
     if (!H->near_generated && H->near_ld / 32 > 16)
         return fail(HTLR_EUNSUPPORTED,
                     "stored dense leaf blocks above 512 points are not supported (use "
@@ -1058,6 +1063,51 @@ static int build(htlr_handle *H, const htlr_grid *grid, const htlr_options *o)
                                 cudaMemcpyHostToDevice, s));
         HTLR_CK(cudaStreamSynchronize(s));
     }
+    // generated near field on the tensor cores: per leaf its first 16-source stage of
+    // packed w u, and the (leaf, tile of near_tc_tile_rows() rows) items, heaviest first
+    if (H->near_generated && H->near_prec == kPrecTF32X3) {
+        const int nleaf = 1 << (d * L), m1 = (1 << L) - 1;
+        const LevelData &Lf = H->lev[L];
+        std::vector<int> stage0((size_t)nleaf + 1, 0), rows(nleaf);
+        int max_rows = 0;
+        for (int g = 0; g < nleaf; ++g) {
+            int r = 1;
+            for (int k = 0; k < d; ++k) r *= Lf.cnt[k][(g >> (L * k)) & m1];
+            rows[g] = r;
+            max_rows = std::max(max_rows, r);
+            stage0[g + 1] = stage0[g] + (r + 15) / 16;
+        }
+        std::vector<long long> wgt;
+        std::vector<int> it;
+        for (int g = 0; g < nleaf; ++g) {
+            long long st = 0;
+            for (int e = H->near_rowptr[g]; e < H->near_rowptr[g + 1]; ++e)
+                st += stage0[H->near_col[e] + 1] - stage0[H->near_col[e]];
+            for (int tl = 0; tl * near_tc_tile_rows() < rows[g]; ++tl) {
+                it.push_back(g);
+                it.push_back(tl);
+                wgt.push_back(st);
+            }
+        }
+        std::vector<int> ord(wgt.size());
+        for (size_t i = 0; i < ord.size(); ++i) ord[i] = (int)i;
+        std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return wgt[a] > wgt[b]; });
+        std::vector<int> items(it.size());
+        for (size_t i = 0; i < ord.size(); ++i) {
+            items[2 * i] = it[2 * (size_t)ord[i]];
+            items[2 * i + 1] = it[2 * (size_t)ord[i] + 1];
+        }
+        H->ntc_nitems = (int)ord.size();
+        H->ntc_max_rows_pad = round_up(max_rows, 16);
+        if (dalloc(H, &H->d_ntc_stage0, stage0.size()) || dalloc(H, &H->d_ntc_items, items.size()) ||
+            dalloc(H, &H->d_ntc_wu, (size_t)stage0[nleaf] * 512) || dalloc(H, &H->d_ntc_counter, 1))
+            return HTLR_ECUDA;
+        HTLR_CK(cudaMemcpyAsync(H->d_ntc_stage0, stage0.data(), sizeof(int) * stage0.size(),
+                                cudaMemcpyHostToDevice, s));
+        HTLR_CK(cudaMemcpyAsync(H->d_ntc_items, items.data(), sizeof(int) * items.size(),
+                                cudaMemcpyHostToDevice, s));
+        HTLR_CK(cudaStreamSynchronize(s));
+    }
     H->max_cols = max_cols;
     H->task_bytes = kTaskBytes;
     if (int rc = build_tasks(H, kTaskBytes, s)) return rc;
@@ -1211,6 +1261,40 @@ int launch_near_gen_all(const htlr_handle *H, const double *uc, double *fc, int 
     const int d = H->d, n = H->n, L = H->L;
     const long long N = (long long)ipow(n, d);
     int launches = 0;
+    if (H->near_prec == kPrecTF32X3) {
+        // tensor cores: 16 right-hand sides per launch (packing of w u, then the product)
+        NearTcArgs t{};
+        t.k = H->kern;
+        t.d = d;
+        t.n = n;
+        t.L = L;
+        t.leafg = level_geom(H, L);
+        t.coords = H->d_coords;
+        t.width = H->d_width;
+        t.diag = H->d_diagpts;
+        t.a = H->d_a;
+        t.rowptr = H->d_near_rowptr;
+        t.col = H->d_near_col;
+        t.stage0 = H->d_ntc_stage0;
+        t.items = H->d_ntc_items;
+        t.nitems = H->ntc_nitems;
+        t.wu = H->d_ntc_wu;
+        t.u = uc;
+        t.ldu = N;
+        t.f = fc;
+        t.ldf = N;
+        t.max_rows_pad = H->ntc_max_rows_pad;
+        t.counter = H->d_ntc_counter;
+        t.err = H->d_err;
+        t.wait_cycles = H->tc_wait_cycles;
+        for (int r0 = 0; r0 < nh; r0 += 16) {
+            t.r0 = r0;
+            t.nr = std::min(16, nh - r0);
+            launch_near_tc(t, s);
+            launches += 2;
+        }
+        return launches;
+    }
     {
         NearGenArgs g{};
         g.k = H->kern;
@@ -1527,7 +1611,7 @@ int htlr_construct_ex(htlr_handle **out, const htlr_kernel *k, int d, int n, con
     if (o && o->tc_wait_cycles < 0) return fail(HTLR_EINVAL, "tc_wait_cycles must be >= 0");
     if (o && (o->orth < -1 || o->orth > 1)) return fail(HTLR_EINVAL, "orth must be -1, 0 or 1");
     if (o && (o->far_precision < 0 || o->far_precision > 3 || o->near_precision < 0 ||
-              o->near_precision > 3))
+              o->near_precision > 4))
         return fail(HTLR_EINVAL, "precisions must be HTLR_PREC_FP64, _DF64, _FP32 or _BF16X6");
 
     htlr_handle *H = nullptr;

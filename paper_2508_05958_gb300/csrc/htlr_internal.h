@@ -33,7 +33,7 @@ constexpr int kMaxP = 16;
 enum DevErr : int { kDevOk = 0, kDevBadIndex = 1, kDevBadTask = 2, kDevTimeout = 3 };
 
 // Arithmetic of a block list (same values as the public htlr_precision enum).
-enum Prec : int { kPrecFP64 = 0, kPrecDF64 = 1, kPrecFP32 = 2, kPrecBF16X6 = 3 };
+enum Prec : int { kPrecFP64 = 0, kPrecDF64 = 1, kPrecFP32 = 2, kPrecBF16X6 = 3, kPrecTF32X3 = 4 };
 
 // Bytes of one block element in memory for a precision.
 inline size_t prec_bytes(int prec) { return prec == kPrecFP32 ? 4 : 8; }
@@ -174,6 +174,12 @@ struct htlr_handle {
     std::vector<htlr::int4v> h_near_cls;
     int *d_near_order[3] = {nullptr, nullptr, nullptr};
     int *d_grp_counter = nullptr;    // one per level + 1 (grouped tensor-core launches)
+    // generated near field on the tensor cores (near_prec kPrecTF32X3)
+    int *d_ntc_stage0 = nullptr;     // per leaf: first stage of its packed sources
+    int *d_ntc_items = nullptr;      // (leaf, tile) pairs, heaviest first
+    int ntc_nitems = 0, ntc_max_rows_pad = 0;
+    float *d_ntc_wu = nullptr;       // packed w u, two TF32 terms, 16 RHS
+    int *d_ntc_counter = nullptr;
     uint16_t *d_Ug = nullptr;
     htlr::TmapBytes near_tmap[3];
     std::vector<int> near_row_task_tc;
@@ -331,6 +337,36 @@ struct NearGenArgs {
     int max_rows;
 };
 void launch_near_generated(int prec, const NearGenArgs &a, cudaStream_t s);
+// ---- near_tc.cu: generated near field on the tensor cores (kPrecTF32X3) ----
+// The same product as NearGenArgs for 16 right-hand sides (r0 .. r0 + nr - 1): kernel
+// values generated per pair into tensor memory as two TF32 terms, times w_j u_j packed as
+// two TF32 terms per source (`wu`, refilled by the launch), kind::tf32 MMAs.
+struct NearTcArgs {
+    KernelDesc k;
+    int d, n, L;
+    LevelGeom leafg;
+    const double *coords;  // d * n
+    const double *width;   // d * n cell widths
+    const double *diag;    // N values: K_ii w_i
+    const double *a;       // N values or null
+    const int *rowptr, *col;
+    const int *stage0;     // per leaf: first 16-source stage of its packed sources (nleaf + 1)
+    const int *items;      // (leaf, 128-row tile) pairs, heaviest first
+    int nitems;
+    float *wu;             // stage0[nleaf] x 512 floats
+    const double *u;
+    long long ldu;
+    double *f;
+    long long ldf;
+    int r0, nr;
+    int max_rows_pad;      // largest leaf, rounded up to 16 points
+    int *counter;          // next item (reset before each launch)
+    int *err;
+    long long wait_cycles;
+};
+void launch_near_tc(const NearTcArgs &a, cudaStream_t s);
+// Rows of one near_tc item (a tile of a leaf's rows, taken by one warpgroup).
+int near_tc_tile_rows();
 // ---- tc_group.cu: grouped tensor-core stream for SHARED block lists ----
 struct TcgArgs {
     const int4 *offs;                  // class offset lists (o1, o2, o3, block id)

@@ -18,7 +18,7 @@ HTLR_OK, HTLR_EINVAL, HTLR_ENOMEM, HTLR_ECUDA, HTLR_EUNSUPPORTED, HTLR_ETIMEOUT,
 K_LOG, K_INV_R, K_EXP_R, K_GAUSS, K_POLY, K_CONST = range(6)
 GRID_UNIFORM, GRID_TENSOR = 0, 1
 STORE_AUTO, STORE_STORED, STORE_SHARED = 0, 1, 2
-PREC_FP64, PREC_DF64, PREC_FP32, PREC_BF16X6 = 0, 1, 2, 3
+PREC_FP64, PREC_DF64, PREC_FP32, PREC_BF16X6, PREC_TF32X3 = 0, 1, 2, 3, 4
 MAX_LEVELS = 16
 
 NUM_STAGES = 5

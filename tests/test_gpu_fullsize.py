@@ -186,5 +186,12 @@ def test_c4_tensor_core_far_fp32_near(c4):
     assert info["storage"] == 3 and info["tc_grouped"] == (1 << 2) | (1 << 3) | (1 << 4)
 
 
+def test_c4_tensor_cores_far_and_near(c4):
+    """The bench's c4 mode: BF16X6 far field on the grouped kernel, the generated near
+    field on the tensor cores (TF32X3)."""
+    info = c4.check(MIXED_TOL, C4_INTERP + MIXED_TOL, far_precision=3, near_precision=4)
+    assert info["storage"] == 3 and info["near_precision"] == 4
+
+
 def test_c4_tensor_core_far_fp64_near(c4):
     c4.check(MIXED_TOL, C4_INTERP + MIXED_TOL, far_precision=3, near_precision=0)

@@ -405,6 +405,72 @@ def test_tensor_core_rejects_unsupported_mixes():
     with pytest.raises(htlr.HTLRError) as ei:
         htlr.htlr_construct(1, 3, 16, 4, 4, 1.0, storage=2, far_precision=0, near_precision=3)
     assert ei.value.code == htlr.HTLR_EUNSUPPORTED
+    # the TF32X3 near field is generated: refused with held dense blocks, and not a far field
+    for storage in (1, 2):
+        with pytest.raises(htlr.HTLRError) as ei:
+            htlr.htlr_construct(1, 3, 16, 4, 4, 1.0, storage=storage, near_precision=4)
+        assert ei.value.code == htlr.HTLR_EUNSUPPORTED
+    for far, near in ((4, 0), (0, 5)):
+        with pytest.raises(htlr.HTLRError) as ei:
+            htlr.htlr_construct(1, 3, 16, 4, 4, 1.0, far_precision=far, near_precision=near)
+        assert ei.value.code == htlr.HTLR_EINVAL
+
+
+# ----------------------------------------------------------------------------------
+# Generated near field on the tensor cores (TF32X3): kernel values generated per pair
+# into tensor memory as two TF32 terms, times w u packed as two TF32 terms, 16 RHS a pass
+# ----------------------------------------------------------------------------------
+@pytest.mark.parametrize("ktype,kparam,nrhs", [(2, 0.0, 16), (1, 0.0, 5), (3, 0.3, 21),
+                                               (0, 0.0, 16), (4, 2.0, 3)])
+def test_tf32x3_generated_near_tensor_grid(oracle, ktype, kparam, nrhs):
+    """Leaves of 7-9 points per dimension (343-729 rows: three to six 128-row tiles, the
+    last one ragged), 16-source stages with a padded tail per source leaf, RHS counts of
+    one full pass, one padded pass and two passes, and every branch of the generator
+    (exp(-r) packed; 1/r; Gaussian; log; the polynomial test kernel)."""
+    from paper_2508_05958_gb300.workloads import Workload
+    w = Workload("tl", d=3, n=32, ktype=ktype, leaf=8, p=5, eta=1.0, kparam=kparam, seed=34)
+    grid = _qgrid(3, 32, seed=9)
+    u = w.u(nrhs=nrhs)
+    f, info = _gpu_tensor(w, grid, u, far_precision=0, near_precision=4)
+    assert info["storage"] == 3 and info["near_precision"] == 4
+    ref = oracle.HTLR(3, 32, ktype, 8, 5, 1.0, grid=grid, orth=False, param=kparam).matvec(u)
+    assert rel(f, ref) < TC_TOL
+
+
+@pytest.mark.parametrize("storage", [0, 3])
+def test_tf32x3_uniform_grid_generated(oracle, storage):
+    """Uniform grid, 1/r with a(x) = 1 + sin (64-point leaves: one ragged tile); AUTO
+    storage generates the near field when its precision is TF32X3."""
+    from paper_2508_05958_gb300.workloads import workload
+    w = workload("c2", n=16)
+    u = w.u(nrhs=16)
+    f, info = gpu_matvec(w, u, storage=storage, near_precision=4)
+    assert info["storage"] == 3 and info["unique_near"] == 0
+    ref, _ = _oracle_htlr(oracle, w, u)
+    assert rel(f, ref) < TC_TOL
+
+
+def test_tf32x3_2d_log_kernel(oracle):
+    """2D single-layer potential, leaves of 16^2 = 256 points (two full tiles)."""
+    from paper_2508_05958_gb300.workloads import Workload
+    w = Workload("k", d=2, n=128, ktype=0, leaf=16, p=6, eta=math.sqrt(2),
+                 kscale=-1 / (2 * math.pi), a_kind="one", seed=6)
+    u = w.u(nrhs=16)
+    f, info = gpu_matvec(w, u, storage=3, near_precision=4)
+    ref, _ = _oracle_htlr(oracle, w, u)
+    assert rel(f, ref) < TC_TOL
+
+
+def test_tf32x3_near_with_tensor_core_far(oracle):
+    """Both fields on the tensor cores: BF16X6 far (grouped kernel on the tensor grid's
+    shared cores), TF32X3 generated near."""
+    from paper_2508_05958_gb300.workloads import Workload
+    w = Workload("tq", d=3, n=32, ktype=2, leaf=4, p=4, eta=1.0, seed=33)
+    grid = _qgrid(3, 32, seed=9)
+    u = w.u(nrhs=32)
+    f, info = _gpu_tensor(w, grid, u, far_precision=3, near_precision=4)
+    ref = oracle.HTLR(3, 32, 2, 4, 4, 1.0, grid=grid, orth=False).matvec(u)
+    assert rel(f, ref) < TC_TOL
 
 
 # ----------------------------------------------------------------------------------

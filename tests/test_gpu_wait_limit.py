@@ -89,3 +89,32 @@ def test_wait_limit_rejects_negative():
         htlr.htlr_construct(1, 3, 16, 4, 4, 1.0, storage=2, far_precision=3, near_precision=3,
                             tc_wait_cycles=-1)
     assert ei.value.code == htlr.HTLR_EINVAL
+
+
+def test_generated_near_field_on_tensor_cores_times_out_and_recovers(oracle):
+    """The TF32X3 generated near field: its drains and its MMA thread wait with the same
+    bounded limit."""
+    import torch
+    from paper_2508_05958_gb300 import htlr
+    from paper_2508_05958_gb300.workloads import workload
+    w = workload("c2", n=16)
+    u = w.u(nrhs=16)
+    H = htlr.htlr_construct(w.ktype, w.d, w.n, w.leaf, w.p, w.eta, a=w.a(), storage=3,
+                            near_precision=4, tc_wait_cycles=8)
+    try:
+        ud = torch.from_numpy(np.ascontiguousarray(u.T)).cuda()
+        fd = torch.full_like(ud, float("nan"))
+        htlr.htlr_matvec(H, ud, fd, 16)
+        with pytest.raises(htlr.HTLRError) as ei:
+            htlr.htlr_sync(H)
+        assert ei.value.code == htlr.HTLR_ETIMEOUT
+        htlr.htlr_sync(H)
+        htlr.htlr_set_wait_limit(H, 0)
+        fd.fill_(float("nan"))
+        htlr.htlr_matvec(H, ud, fd, 16)
+        htlr.htlr_sync(H)
+        f = fd.cpu().numpy().T.copy()
+    finally:
+        htlr.htlr_free(H)
+    ref = oracle.HTLR(w.d, w.n, w.ktype, w.leaf, w.p, w.eta, a=w.a()).matvec(u)
+    assert rel(f, ref) < TC_TOL

@@ -94,7 +94,8 @@ def test_noalloc_makes_no_device_allocation(lib):
 
 def _paths():
     """Operators that take the other paths of the allocation-free matvec: a generated near
-    field on a quasi-uniform tensor grid, df64 and FP32 block lists, SHARED storage."""
+    field on a quasi-uniform tensor grid (on the CUDA cores, and on the tensor cores in
+    two passes of 16 RHS), df64 and FP32 block lists, SHARED storage."""
     from paper_2508_05958_gb300.workloads import Workload, quasi_uniform_tensor_grid, workload
     tq = Workload("tq", d=3, n=16, ktype=2, leaf=4, p=4, eta=1.0, seed=41)
     return [
@@ -103,10 +104,12 @@ def _paths():
         ("FP32 far / df64 near, SHARED", workload("c2", n=16),
          dict(storage=2, far_precision=2, near_precision=1), 4),
         ("FP64, SHARED", workload("c1"), dict(storage=2), 1),
+        ("TF32X3 generated near, tensor grid", tq,
+         dict(grid=quasi_uniform_tensor_grid(3, 16, 9), near_precision=4), 17),
     ]
 
 
-@pytest.mark.parametrize("case", range(4))
+@pytest.mark.parametrize("case", range(5))
 def test_noalloc_other_paths_equal_matvec_bitwise(lib, case):
     """The allocation-free matvec runs the same kernels on the same data in the same
     order as htlr_matvec, only with other scratch addresses: the results are equal bit for
