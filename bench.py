@@ -272,7 +272,7 @@ ALU_PEAK = {0: 152 * 2 * 2.07e9, 1: 152 * 128 * 2.07e9 / 12, 2: 152 * 128 * 2.07
 
 
 # DRAM traffic (read + write bytes) of one launch of the dominant kernel, taken with ncu
-# on the same workload and kernel build (see profiles/stream_kernel_df64_c2_launches.md);
+# on the same workload and kernel build (profiles/stream_kernel_df64_c2_launches.md);
 # keyed by (workload, storage, far precision, near precision, RHS).
 MEASURED_TRAFFIC = {("c2", 1, 1, 1, 1): 5804274688 + 13374976}
 
