@@ -545,3 +545,19 @@ def test_large_2d_boxes_match_oracle_rows(oracle, case, prec):
     ref = oracle.htlr_rows(w.d, w.n, w.ktype, w.leaf, w.p, w.eta, u, rows, param=w.kparam,
                            a=w.a())
     assert rel(f[rows], ref) < TOL
+
+
+def test_tf32x3_largest_leaves_2d(oracle):
+    """The largest leaves the library takes (32^2 = 1024 points: eight 128-row tiles, the
+    largest coordinate buffer of the generating warpgroups), 2D Gaussian, with two passes
+    of 16 RHS of which the second is padded."""
+    from paper_2508_05958_gb300.workloads import Workload
+    w = Workload("leaf32", d=2, n=256, ktype=3, leaf=32, p=6, eta=math.sqrt(2.0),
+                 kparam=math.sqrt(2.0), a_kind="one", seed=53)
+    u = w.u(nrhs=20)
+    rows = w.sample_rows(24, seed=54)
+    f, info = gpu_matvec(w, u, storage=3, near_precision=4)
+    assert info["storage"] == 3 and info["near_precision"] == 4
+    ref = oracle.htlr_rows(w.d, w.n, w.ktype, w.leaf, w.p, w.eta, u, rows, param=w.kparam,
+                           a=w.a())
+    assert rel(f[rows], ref) < TC_TOL
