@@ -199,7 +199,9 @@ void launch_up(int d, int n, const LevelGeom &g, const double *u, int nrhs_here,
     // u staged 4096 values at a time
     int slab = n3;
     while (slab > 1 && (long long)pe * mc * slab > 8192) slab = (slab + 1) / 2;
-    const int urows = std::max(1, 4096 / mc);
+    // rows of u staged at a time: at most 4096 values, and no more rows than a slab holds
+    // (c2 x slab <= mc x slab), so that small boxes leave room for more CTAs per SM
+    const int urows = std::max(1, std::min(4096 / mc, mc * slab));
     const int vsm = 3 * mc * pe <= 8192 ? 1 : 0;   // factors staged when within 64 KB
     size_t smem = sizeof(double) * ((vsm ? (size_t)3 * mc * pe : 0) + (size_t)pe * mc * slab +
                                     (size_t)pe * pe * n3 + (size_t)mc * urows);

@@ -39,8 +39,8 @@
 // each), and release the buffer.  The drain of one segment overlaps the MMAs of the
 // next.  At the end of a pass the sums are written as the FP64 partials of the group's
 // rows.
-// Groups are taken heaviest first from an atomic counter over a host-sorted order, so
-// the SMs finish together.  Every wait is bounded (A.wait_cycles SM cycles): on timeout
+// Work items, one pass of one group each, are taken heaviest first from an atomic counter
+// over a host-sorted order, so the SMs finish together.  Every wait is bounded (A.wait_cycles SM cycles): on timeout
 // the kernel records kDevTimeout, waits (with the long default limit) for the copies and
 // MMAs it has issued, frees TMEM and returns.
 #include <cuda.h>
@@ -289,12 +289,16 @@ __global__ void __launch_bounds__(kGThreads, 1)
     bool ok = true;
 
     while (true) {
-        // next group, heaviest first (dynamic: an atomic counter over a host-sorted order)
+        // next work item, heaviest first (dynamic: an atomic counter over a host-sorted
+        // order).  An item is one pass over N of one group: the passes of a group write
+        // disjoint columns of its partial rows, so they run on different CTAs, which
+        // doubles the items of two-pass block lists (levels with few groups fill the SMs)
         if (tid == 0) cur_group = atomicAdd(A.counter, 1);
         __syncthreads();
         const long long gi = cur_group;
-        if (gi >= A.ngroups) break;
-        const long long grp = A.order[gi];
+        if (gi >= A.ngroups * passes) break;
+        const long long grp = A.order[gi / passes];
+        const int ps_lo = (int)(gi % passes), ps_hi = ps_lo + 1;   // this item's pass
         // group -> (b23, c1, j): tau_0 = (c1 + 2 j G, b2, b3)
         const int j = (int)(grp % A.nq);
         const long long rest = grp / A.nq;
@@ -329,7 +333,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
         if (tid == 32 && total > 0) {
             // producer: stage it_p goes to cross slot it_p % Sc and lead slot it_p % Sl, each
             // refilled once the MMAs that read its previous stage are done
-            for (int ps = 0; ps < passes && !abort_flag; ++ps) {
+            for (int ps = ps_lo; ps < ps_hi && !abort_flag; ++ps) {
                 int oi = 0, ch = 0;                    // offset (in valid order) and chunk
                 for (long long q = 0; q < total; ++q, ++it_p) {
                     const int c = pc, l = pl;
@@ -404,7 +408,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
             const uint32_t a16 = a_split_bytes >> 4, b16 = b_split_bytes >> 4;
             const uint32_t lead16 = lead_bytes >> 4, cross16 = cross_bytes >> 4;
             const uint32_t cring16 = (uint32_t)((size_t)Sl * lead_bytes) >> 4;
-            for (int ps = 0; ps < passes && !abort_flag; ++ps)
+            for (int ps = ps_lo; ps < ps_hi && !abort_flag; ++ps)
                 for (long long q0 = 0; q0 < total; q0 += F) {
                     const int nq = (int)(total - q0 < F ? total - q0 : F);
                     const uint32_t buf = sc_m & 1;
@@ -469,7 +473,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
                 return A.part + A.tasks[ta].part + (long long)r * A.ld;
             };
             const int FL = A.flush_segs;
-            for (int ps = 0; ps < passes; ++ps) {
+            for (int ps = ps_lo; ps < ps_hi; ++ps) {
                 // FP32 sums of the drained segments; every FL segments (and after the last
                 // one) they go to the row's FP64 partial: stored by the first flush of the
                 // pass, then added by fire-and-forget L2 reductions, so the drain never waits
@@ -585,7 +589,8 @@ void launch_tc_group(const TcgArgs &a, const void *tmap, cudaStream_t s)
     cudaMemsetAsync(a.counter, 0, sizeof(int), s);
     const size_t smem = tcg_lead_bytes(a.Nw / 8) * a.lead_stages + tcg_cross_bytes(a.Nw / 8) * a.stages;
     cudaFuncSetAttribute(tc_group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const int grid = a.ngroups < 152 ? (int)a.ngroups : 152;
+    const long long items = a.ngroups * a.passes;   // (group, pass) work items
+    const int grid = items < 152 ? (int)items : 152;
     tc_group_kernel<<<grid, kGThreads, smem, s>>>(*static_cast<const CUtensorMap *>(tmap), a);
 }
 
