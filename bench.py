@@ -408,11 +408,11 @@ SUITE = {
 # FLOPs of the full-size matvec, since every launch streams its cores and sources per
 # group and offset.  None: not captured for the current kernel.
 TRAFFIC_PER_TENSOR_FLOP = {
-    # c3_n64: 18.54 GB of DRAM reads + writes over the three grouped launches of one matvec,
+    # c3_n64: 18.68 GB of DRAM reads + writes over the three grouped launches of one matvec,
     # 1.482e13 executed BF16 FLOPs (profiles/tc_group_kernel_c3n64_ncu.md)
-    "c3": 18.542e9 / 1.4819e13,
-    # c4_n64: 16.11 GB over the two grouped launches, 9.680e12 executed FLOPs
-    "c4": 16.113e9 / 9.6803e12,
+    "c3": 18.683e9 / 1.4819e13,
+    # c4_n64: 19.32 GB over the two grouped launches, 9.680e12 executed FLOPs
+    "c4": 19.324e9 / 9.6803e12,
 }
 
 
