@@ -66,6 +66,27 @@ def test_generated_near_roofline_counts_pairs_times_rhs():
     assert roof["kernel_evaluations_per_s"] == pytest.approx(1e7 / 2e-3, rel=1e-12)
 
 
+@pytest.mark.parametrize("ktype,sfu", [(2, 2), (1, 1), (3, 1), (0, 1), (4, None)])
+def test_tensor_core_near_roofline_is_the_sfu_rate(ktype, sfu):
+    """The generated near field on the tensor cores: kernel values per second against
+    152 SMs x 2.07 GHz x 16 SFU operations per clock, divided by the SFU operations one
+    value costs (exp(-r): rsqrt and ex2; 1/r, the Gaussian, log: one); the polynomial
+    test kernel uses none and has no SFU bound."""
+    from paper_2508_05958_gb300.workloads import Workload
+    w = Workload("k", d=3, n=16, ktype=ktype, leaf=4, p=3, eta=1.0)
+    info = {"near_precision": 4, "storage": 3, "near_point_pairs": 2_000_000}
+    roof = bench.near_tc_roofline(info, w, 21, 4.0)
+    assert roof["achieved"] == pytest.approx(2e6 / 4e-3 / 1e9, rel=1e-12)
+    assert roof["multiply_adds_per_launch"] == 21 * 2_000_000
+    # two passes of 16 right-hand sides, three TF32 products per value and RHS
+    assert roof["tf32_tensor_flops_per_launch"] == 2e6 * 16 * 2 * 3 * 2
+    if sfu is None:
+        assert roof["peak"] is None and roof["frac"] is None
+    else:
+        assert roof["peak"] == pytest.approx(152 * 16 * 2.07e9 / sfu / 1e9, rel=1e-12)
+        assert roof["frac"] == pytest.approx(roof["achieved"] / roof["peak"], rel=1e-12)
+
+
 def test_column_relative_errors():
     ref = np.array([[3.0, 1.0], [4.0, 0.0]])
     f = ref + np.array([[0.0, 0.5], [0.5, 0.0]])
