@@ -195,13 +195,13 @@ void launch_up(int d, int n, const LevelGeom &g, const double *u, int nrhs_here,
     const int nbox = 1 << (d * g.level);
     const int mc = g.maxcnt, pe = g.pe;
     const int n3 = (d == 3) ? mc : 1;
-    // slab of the last dimension so that the mode-1 buffer stays within 64 KB, and rows of
-    // u staged 4096 values at a time
+    // slab of the last dimension so that the mode-1 buffer stays within 1024 values, and
+    // rows of u staged at most 1024 values at a time (no more rows than a slab holds,
+    // c2 x slab <= mc x slab): large boxes then take about 28 KB of shared memory and run
+    // 8 CTAs per SM instead of 4 (their mode products wait on shared-memory latency)
     int slab = n3;
-    while (slab > 1 && (long long)pe * mc * slab > 8192) slab = (slab + 1) / 2;
-    // rows of u staged at a time: at most 4096 values, and no more rows than a slab holds
-    // (c2 x slab <= mc x slab), so that small boxes leave room for more CTAs per SM
-    const int urows = std::max(1, std::min(4096 / mc, mc * slab));
+    while (slab > 1 && (long long)pe * mc * slab > 1024) slab = (slab + 1) / 2;
+    const int urows = std::max(1, std::min(1024 / mc, mc * slab));
     const int vsm = 3 * mc * pe <= 8192 ? 1 : 0;   // factors staged when within 64 KB
     size_t smem = sizeof(double) * ((vsm ? (size_t)3 * mc * pe : 0) + (size_t)pe * mc * slab +
                                     (size_t)pe * pe * n3 + (size_t)mc * urows);
