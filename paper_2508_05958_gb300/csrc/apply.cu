@@ -275,11 +275,12 @@ void launch_reduce_far(int nbox, int pd, int ld, int nrc, int nrhs_here, const i
 // ancestor; written once, in natural order.  The base is the sum of the leaf's
 // dense-block partials in task order [+ a u], or the generated near field already in f.
 // ---------------------------------------------------------------------------------
-constexpr int kOutPer = 8;  // rows per thread: leaves of up to 8 * 256 points
-
-template <class AR>
+// PER: row slots per thread (leaves of up to PER * 256 points), a template argument so
+// that the slots stay in registers and only as many as the largest leaf needs are held.
+template <class AR, int PER>
 __global__ void __launch_bounds__(256) out_kernel(OutArgs A)
 {
+    constexpr int kOutPer = PER;
     using T = typename AR::T;
     extern __shared__ __align__(16) unsigned char out_sm[];
     T *sm = reinterpret_cast<T *>(out_sm);
@@ -292,6 +293,7 @@ __global__ void __launch_bounds__(256) out_kernel(OutArgs A)
     double base[kOutPer];        // near field (+ a u + diagonal), FP64
     T far[kOutPer];              // far field of all levels, in the arithmetic AR
     long long nat[kOutPer];
+#pragma unroll
     for (int m = 0; m < kOutPer; ++m) {
         base[m] = 0.0;
         far[m] = AR::zero();
@@ -362,6 +364,7 @@ __global__ void __launch_bounds__(256) out_kernel(OutArgs A)
             Z2[idx] = acc;
         }
         __syncthreads();
+#pragma unroll
         for (int m = 0; m < kOutPer; ++m) {
             const int i = threadIdx.x + blockDim.x * m;
             if (m < per && i < rows) {
@@ -373,8 +376,28 @@ __global__ void __launch_bounds__(256) out_kernel(OutArgs A)
         }
         __syncthreads();
     }
+#pragma unroll
     for (int m = 0; m < kOutPer; ++m)
         if (nat[m] >= 0) A.f[nat[m] + A.ldf * r] = base[m] + AR::to(far[m]);
+}
+
+template <class AR, int PER>
+static void launch_out_per(const OutArgs &a, size_t smem, dim3 grid, int threads, cudaStream_t s)
+{
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(out_kernel<AR, PER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    out_kernel<AR, PER><<<grid, threads, smem, s>>>(a);
+}
+
+template <class AR>
+static void launch_out_ar(const OutArgs &a, int per, size_t smem, dim3 grid, int threads,
+                          cudaStream_t s)
+{
+    if (per <= 1) launch_out_per<AR, 1>(a, smem, grid, threads, s);
+    else if (per <= 2) launch_out_per<AR, 2>(a, smem, grid, threads, s);
+    else if (per <= 4) launch_out_per<AR, 4>(a, smem, grid, threads, s);
+    else launch_out_per<AR, 8>(a, smem, grid, threads, s);
 }
 
 void launch_out(const OutArgs &a, int max_rows, cudaStream_t s, bool df64)
@@ -390,18 +413,10 @@ void launch_out(const OutArgs &a, int max_rows, cudaStream_t s, bool df64)
     smem *= sizeof(double);
     if (smem == 0) smem = sizeof(double);
     int threads = max_rows < 256 ? ((max_rows + 31) / 32) * 32 : 256;
+    const int per = (max_rows + threads - 1) / threads;   // row slots per thread, <= 8
     dim3 grid(1 << (a.d * a.L), a.nrhs);
-    if (df64) {
-        if (smem > 48 * 1024)
-            cudaFuncSetAttribute(out_kernel<ArithDF64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-        out_kernel<ArithDF64><<<grid, threads, smem, s>>>(a);
-    } else {
-        if (smem > 48 * 1024)
-            cudaFuncSetAttribute(out_kernel<ArithFP64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-        out_kernel<ArithFP64><<<grid, threads, smem, s>>>(a);
-    }
+    if (df64) launch_out_ar<ArithDF64>(a, per, smem, grid, threads, s);
+    else launch_out_ar<ArithFP64>(a, per, smem, grid, threads, s);
 }
 
 }  // namespace htlr
