@@ -57,7 +57,9 @@ using namespace tcc;
 namespace {
 
 constexpr int kSlots = 3;                       // A (tensor memory) and B (shared) slots
-constexpr int kR = 1;                           // rows per generating thread (tiles per warpgroup)
+// rows per generating thread (tiles per warpgroup); two, with two warpgroups, measured
+// slower than one with four: the generation needs warps more than per-thread parallelism
+constexpr int kR = 1;
 constexpr int kWG = 4 / kR;                     // generating warpgroups per CTA
 constexpr int kGenThreads = 128 * kWG;
 constexpr int kThreads = kGenThreads + 32 * kWG;   // + one MMA warp per warpgroup
@@ -294,7 +296,7 @@ __global__ void __launch_bounds__(kThreads, 1) near_tc_kernel(NearTcArgs A)
                 const uint32_t buf = mseg & 1;
                 const uint64_t bd = smem_desc(ring + (uint32_t)a * kStageBytes, 128, 256);
 #pragma unroll
-                for (int m = 0; m < kR; ++m) {   // tile m: columns g kWgCols + 128 m
+                for (int m = 0; m < kR; ++m) {   // tile m: columns g kWgCols + kTileCols m
                     const uint32_t tt = tmem + (uint32_t)(g * kWgCols + kTileCols * m);
                     const uint32_t dt = tt + kAccCol + 16u * buf, ta = tt + 32u * a;
                     mma_tf32_ts(dt, ta + 16, bd, idesc, (fl & kInfoFirst) ? 0u : 1u);   // a2 b1
